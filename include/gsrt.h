@@ -1,0 +1,211 @@
+/*
+ * gsrt.h -- C ABI of the GB300 library for stochastic ray tracing of
+ * transparent 3D Gaussians (arXiv 2504.06598).
+ *
+ * One ray walks a bounding volume hierarchy over the Gaussians' bounding
+ * boxes once (Sec. 3.2), evaluates each overlapped Gaussian's 1D Gaussian
+ * along the ray (Sec. 3.1), accepts it at random with probability alpha
+ * (Eq. 4, Alg. 1), keeps the closest accepted intersection (Eq. 6) or N of
+ * them (Eq. 7, Sec. 3.5), and shades it with view-dependent spherical
+ * harmonics. The result is an unbiased estimate of the depth-sorted blend
+ * (Eq. 3).
+ *
+ * Conventions shared by every call
+ *   - Pointers named in a struct or argument list as "device" must point to
+ *     CUDA device memory of the current device; "host" pointers to host
+ *     memory. Arrays are dense, row-major, 16-byte aligned (as returned by
+ *     cudaMalloc or a PyTorch allocation).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Every call only enqueues work on it and returns without
+ *     waiting, except where stated.
+ *   - Argument errors are returned before anything is enqueued and leave
+ *     all outputs untouched. gs_last_error() then describes the problem.
+ *   - Errors found by a kernel (stack overflow, traversal step limit,
+ *     non-finite parameters) are recorded in a status word owned by the BVH
+ *     handle and are returned by gs_bvh_sync_status().
+ *   - No call throws, traps, or waits on the device without a bound.
+ *
+ * Random draws: xi for (ray r, Gaussian g, sample s) is lane (s & 3) of
+ * Philox-4x32-10 with key (seed low word, seed high word) and counter
+ * (r, g, s >> 2, stream_tag), mapped to [0,1) as (u >> 8) * 2^-24. A hit
+ * is accepted iff xi < alpha. Results therefore depend only on (seed, ray
+ * id, Gaussian id, sample index), not on the hierarchy or launch shape.
+ */
+#ifndef GSRT_H
+#define GSRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gs_status {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1,    /* a pointer, size or option was rejected */
+    GS_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    GS_ERR_OOM = 3,            /* device allocation failed */
+    GS_ERR_STACK_OVERFLOW = 4, /* a ray needed more than stack_depth entries */
+    GS_ERR_STEP_LIMIT = 5,     /* a ray exceeded the traversal step bound */
+    GS_ERR_NONFINITE = 6,      /* a Gaussian parameter was NaN or infinite */
+    GS_ERR_NO_DEVICE = 7       /* no CUDA device is available */
+} gs_status;
+
+/* Storage type of the spherical-harmonic coefficients. */
+enum { GS_SH_F32 = 0, GS_SH_F16 = 1, GS_SH_BF16 = 2 };
+
+/* Gaussian parameters (Eq. 1). All device pointers, caller-owned.
+ *   means          [M][3] float  mu
+ *   log_scales     [M][3] float  S = diag(exp(log_scales))
+ *   quats          [M][4] float  (w,x,y,z), normalised by the library; the
+ *                                 rotation R_q maps local to world and the
+ *                                 paper's R equals R_q^T, so
+ *                                 Sigma = R_q S^2 R_q^T
+ *   opacity_logits [M]    float  opacity = sigmoid(logit)
+ *   sh             [M][K][3]     K = (sh_degree+1)^2 coefficients per
+ *                                 channel, type sh_dtype; colour
+ *                                 c = max(0, k_0 + sum_{l>=1,m} Y_lm(d) k_lm)
+ *                                 with real SH (Condon-Shortley phase),
+ *                                 m = -l..l, d the unit ray direction; the
+ *                                 DC term k_0 is stored pre-multiplied.
+ *   M >= 0, M < 2^31; sh_degree in 0..3. */
+typedef struct gs_gaussians {
+    const float *means;
+    const float *log_scales;
+    const float *quats;
+    const float *opacity_logits;
+    const void *sh;
+    int64_t M;
+    int32_t sh_degree;
+    int32_t sh_dtype;
+} gs_gaussians;
+
+/* Pinhole camera. The ray through pixel (x, y), row 0 at the top, is
+ * defined in float32 by this exact sequence (each operation rounded once,
+ * no fused multiply-add):
+ *   th = (float) tan((double) fov_y_deg * pi / 360)
+ *   f = normalise(look_at - eye), r = normalise(f x up), u = r x f
+ *   s = th / height, ux = (2x + 1 - width) * s, uy = (height - 1 - 2y) * s
+ *   d = normalise((f + ux * r) + uy * u), origin = eye,
+ * normalise(v) = v / sqrt((v.x*v.x + v.y*v.y) + v.z*v.z).
+ * Ray ids are ray_id_offset + y * width + x and must fit in 32 bits. */
+typedef struct gs_pinhole {
+    float eye[3];
+    float look_at[3];
+    float up[3];
+    float fov_y_deg;
+    int32_t width;
+    int32_t height;
+    uint32_t ray_id_offset;
+    int32_t reserved;
+} gs_pinhole;
+
+/* Options of one trace (Alg. 1, Eq. 7).
+ *   spp           passes: full traversals per pixel, >= 1
+ *   n_hits        N, samples kept per traversal: 1, 2, 4 or 8
+ *                 sample index s = pass * n_hits + k
+ *   t_min, t_max  valid ray range, candidates need t_min < t < t_max
+ *   bg            background colour of samples with no accepted hit
+ *   depth_mode    0: depth is the mean of the 1D Gaussian (Sec. 3.1)
+ *   stack_depth   traversal stack entries per ray, 1..64 (0 = 64)
+ *   stream_tag    fourth Philox counter word, separates ray streams
+ *   counters      optional device uint64[4], incremented by the launch:
+ *                 {nodes visited, primitives tested, Philox draws, rays};
+ *                 NULL disables counting (the default fast path). */
+typedef struct gs_trace_params {
+    uint64_t seed;
+    int32_t spp;
+    int32_t n_hits;
+    float t_min;
+    float t_max;
+    float bg[3];
+    int32_t depth_mode;
+    int32_t stack_depth;
+    uint32_t stream_tag;
+    unsigned long long *counters;
+} gs_trace_params;
+
+/* Opaque hierarchy handle: library-owned device buffers holding the
+ * per-Gaussian records (in hierarchy order), the nodes, build scratch and
+ * the device status word. */
+typedef struct gs_bvh gs_bvh;
+
+typedef struct gs_bvh_info {
+    int64_t M;            /* Gaussians indexed */
+    int64_t n_nodes;      /* internal nodes (max(M-1, 1), 0 when M = 0) */
+    int64_t capacity;     /* largest M a rebuild can take without allocating */
+    int64_t device_bytes; /* device memory held by the handle */
+    int32_t node_bytes;   /* bytes per node record */
+    int32_t prim_bytes;   /* bytes per Gaussian record */
+} gs_bvh_info;
+
+/* Build the hierarchy over the Gaussians' bounding boxes (Sec. 3.2; the box
+ * bounds the ellipsoid of Eq. 2 with s = 2 sqrt(2), tightly, then padded
+ * outward so that no valid intersection is lost).
+ *   g      Gaussian parameters (device arrays, read during the call's
+ *          kernels only; SH is not read)
+ *   out    receives a new handle (host pointer to a handle pointer)
+ *   stream build kernels are enqueued here
+ * Allocates the handle's device memory (synchronously). Parameters must be
+ * unchanged until the build's kernels have run. Returns GS_ERR_INVALID_ARG
+ * for bad sizes or pointers, GS_ERR_OOM / GS_ERR_CUDA / GS_ERR_NO_DEVICE on
+ * CUDA failures. Non-finite parameters are reported by gs_bvh_sync_status. */
+gs_status gs_build_bvh(const gs_gaussians *g, gs_bvh **out, void *stream);
+
+/* Rebuild an existing handle for new parameters with M <= capacity, with no
+ * allocation (the usual per-frame call when Gaussians move). Same rules as
+ * gs_build_bvh; M > capacity returns GS_ERR_INVALID_ARG. */
+gs_status gs_bvh_rebuild(gs_bvh *bvh, const gs_gaussians *g, void *stream);
+
+/* Release the handle and its device memory (synchronises the device first).
+ * NULL is accepted. */
+gs_status gs_bvh_free(gs_bvh *bvh);
+
+/* Fill *info (host struct) about the handle. */
+gs_status gs_bvh_get_info(const gs_bvh *bvh, gs_bvh_info *info);
+
+/* Wait for `stream`, then return and clear the device status word: GS_OK or
+ * the first error a build or trace kernel recorded since the last call. */
+gs_status gs_bvh_sync_status(gs_bvh *bvh, void *stream);
+
+/* Copy the hierarchy to host memory for inspection (synchronous).
+ *   nodes_out  host, n_nodes * node_bytes bytes, or NULL
+ *   prims_out  host, M * prim_bytes bytes, or NULL
+ *   codes_out  host uint64[M]: sorted Morton codes, or NULL
+ *   order_out  host uint32[M]: Gaussian id of each leaf position, or NULL
+ * Node record (64 bytes): float box[2][6] as {lo.x,lo.y,lo.z,hi.x,hi.y,
+ * hi.z} of the left then right child, uint32 child[2], uint32 reserved[2];
+ * a child reference with bit 31 set is leaf (ref & 0x7fffffff), else an
+ * internal node index; node 0 is the root. */
+gs_status gs_bvh_export(const gs_bvh *bvh, void *nodes_out, void *prims_out,
+                        uint64_t *codes_out, uint32_t *order_out);
+
+/* Render one pinhole view by stochastic ray tracing (Alg. 1, Eq. 4-7).
+ *   bvh        built from the same Gaussians `g` (unchanged since)
+ *   g          Gaussian parameters; only sh/sh_degree/sh_dtype are read here
+ *   cam        host struct, width and height >= 1
+ *   p          host struct of options
+ *   rgb_out    device float[height][width][3]: mean over spp * n_hits
+ *              samples of the closest accepted hit's colour (bg if none)
+ *   hit_id_out device int32[spp][n_hits][height][width] Gaussian id of each
+ *              sample's hit or -1; NULL to skip
+ *   hit_t_out  device float[spp][n_hits][height][width] depth of each
+ *              sample's hit (ray parameter, d is unit length) or +inf;
+ *              NULL to skip
+ * Deterministic: identical inputs give bit-identical outputs. */
+gs_status gs_trace_stochastic(const gs_bvh *bvh, const gs_gaussians *g, const gs_pinhole *cam,
+                              const gs_trace_params *p, float *rgb_out, int32_t *hit_id_out,
+                              float *hit_t_out, void *stream);
+
+/* Short description of a status code (static string). */
+const char *gs_status_string(gs_status s);
+
+/* Detail of the last error returned on the calling thread (static buffer,
+ * valid until the next call on that thread). */
+const char *gs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSRT_H */

@@ -1,0 +1,284 @@
+"""Stochastic ray tracing of transparent 3D Gaussians on GB300 (sm_103a).
+
+Thin Python binding over the C ABI of ``include/gsrt.h`` (``libgsrt.so``):
+argument marshalling only. PyTorch provides device memory and streams; every
+step of the rendering path runs in the library's CUDA kernels. There is no
+CPU fallback: if the library has not been built, importing the binding's
+entry points raises.
+
+Entry points mirror the C names: :func:`build_bvh` (``gs_build_bvh``),
+:meth:`Bvh.rebuild` (``gs_bvh_rebuild``), :func:`trace_stochastic`
+(``gs_trace_stochastic``).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgsrt.so")
+
+GS_OK = 0
+STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_OOM",
+                4: "GS_ERR_STACK_OVERFLOW", 5: "GS_ERR_STEP_LIMIT", 6: "GS_ERR_NONFINITE",
+                7: "GS_ERR_NO_DEVICE"}
+SH_F32, SH_F16, SH_BF16 = 0, 1, 2
+_SH_DTYPES = {torch.float32: SH_F32, torch.float16: SH_F16, torch.bfloat16: SH_BF16}
+
+
+class GsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+class _Gaussians(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p), ("M", C.c_int64),
+                ("sh_degree", C.c_int32), ("sh_dtype", C.c_int32)]
+
+
+class _Pinhole(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("look_at", C.c_float * 3), ("up", C.c_float * 3),
+                ("fov_y_deg", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("ray_id_offset", C.c_uint32), ("reserved", C.c_int32)]
+
+
+class _TraceParams(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("spp", C.c_int32), ("n_hits", C.c_int32),
+                ("t_min", C.c_float), ("t_max", C.c_float), ("bg", C.c_float * 3),
+                ("depth_mode", C.c_int32), ("stack_depth", C.c_int32),
+                ("stream_tag", C.c_uint32), ("counters", C.c_void_p)]
+
+
+class _BvhInfo(C.Structure):
+    _fields_ = [("M", C.c_int64), ("n_nodes", C.c_int64), ("capacity", C.c_int64),
+                ("device_bytes", C.c_int64), ("node_bytes", C.c_int32),
+                ("prim_bytes", C.c_int32)]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+# Every function the header declares, with its ctypes signature.
+_SIGNATURES = {
+    "gs_build_bvh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_bvh_rebuild": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_bvh_free": (C.c_int, [C.c_void_p]),
+    "gs_bvh_get_info": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "gs_bvh_sync_status": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "gs_bvh_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_trace_stochastic": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_status_string": (C.c_char_p, [C.c_int]),
+    "gs_last_error": (C.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded ``libgsrt.so``. Raises if it has not been built."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libgsrt.so is not built (%s); run "
+                                   "paper_2504_06598_gb300.build.build() first" % LIB_PATH)
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != GS_OK:
+        raise GsError(status, lib().gs_last_error().decode(errors="replace"))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- data
+
+
+class Gaussians:
+    """Device-resident Gaussian parameters in the layout of ``gs_gaussians``."""
+
+    def __init__(self, means, log_scales, quats, opacity_logits, sh, sh_degree: int):
+        def dev(t, dtype=torch.float32):
+            t = torch.as_tensor(t)
+            if not t.is_cuda:
+                t = t.to("cuda")
+            return t.to(dtype).contiguous()
+
+        self.means = dev(means)
+        self.log_scales = dev(log_scales)
+        self.quats = dev(quats)
+        self.opacity_logits = dev(opacity_logits)
+        sh = torch.as_tensor(sh)
+        self.sh = dev(sh, sh.dtype if sh.dtype in _SH_DTYPES else torch.float32)
+        self.sh_degree = int(sh_degree)
+        self.M = int(self.means.shape[0])
+
+    @classmethod
+    def from_cloud(cls, cloud, sh_dtype=torch.float32):
+        return cls(torch.from_numpy(cloud.means), torch.from_numpy(cloud.log_scales),
+                   torch.from_numpy(cloud.quats), torch.from_numpy(cloud.opacity_logits),
+                   torch.from_numpy(cloud.sh).to(sh_dtype), cloud.sh_degree)
+
+    def struct(self) -> _Gaussians:
+        return _Gaussians(self.means.data_ptr(), self.log_scales.data_ptr(),
+                          self.quats.data_ptr(), self.opacity_logits.data_ptr(),
+                          self.sh.data_ptr(), self.M, self.sh_degree, _SH_DTYPES[self.sh.dtype])
+
+
+@dataclass
+class Camera:
+    width: int
+    height: int
+    eye: tuple = (0.0, 0.0, 3.0)
+    look_at: tuple = (0.0, 0.0, 0.0)
+    up: tuple = (0.0, 1.0, 0.0)
+    fov_y_deg: float = 60.0
+    ray_id_offset: int = 0
+
+    def struct(self) -> _Pinhole:
+        s = _Pinhole()
+        s.eye[:] = [float(v) for v in self.eye]
+        s.look_at[:] = [float(v) for v in self.look_at]
+        s.up[:] = [float(v) for v in self.up]
+        s.fov_y_deg = float(self.fov_y_deg)
+        s.width, s.height = int(self.width), int(self.height)
+        s.ray_id_offset = int(self.ray_id_offset)
+        return s
+
+    @classmethod
+    def of(cls, cam):
+        return cls(cam.width, cam.height, tuple(cam.eye), tuple(cam.look_at), tuple(cam.up),
+                   float(cam.fov_y_deg), int(cam.ray_id_offset))
+
+
+def _params(seed=0, spp=1, n_hits=1, t_min=0.0, t_max=float("inf"), bg=(0.0, 0.0, 0.0),
+            stack_depth=0, stream_tag=0, counters=None) -> _TraceParams:
+    p = _TraceParams()
+    p.seed = int(seed)
+    p.spp = int(spp)
+    p.n_hits = int(n_hits)
+    p.t_min = float(t_min)
+    p.t_max = float(t_max)
+    p.bg[:] = [float(v) for v in bg]
+    p.depth_mode = 0
+    p.stack_depth = int(stack_depth)
+    p.stream_tag = int(stream_tag)
+    p.counters = None if counters is None else counters.data_ptr()
+    return p
+
+
+# ---------------------------------------------------------------- hierarchy
+
+
+class Bvh:
+    """Owns a ``gs_bvh`` handle (released on :meth:`free` or collection)."""
+
+    def __init__(self, handle: C.c_void_p, M: int):
+        self._h = handle
+        self.M = M
+
+    @property
+    def handle(self):
+        return self._h
+
+    def rebuild(self, g: Gaussians, stream=None):
+        gs = g.struct()
+        _check(lib().gs_bvh_rebuild(self._h, C.byref(gs), _stream_handle(stream)))
+        self.M = g.M
+
+    def info(self) -> dict:
+        i = _BvhInfo()
+        _check(lib().gs_bvh_get_info(self._h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in _BvhInfo._fields_}
+
+    def sync_status(self, stream=None):
+        _check(lib().gs_bvh_sync_status(self._h, _stream_handle(stream)))
+
+    def export(self) -> dict:
+        info = self.info()
+        nn, M = info["n_nodes"], info["M"]
+        nodes = np.zeros((max(nn, 0), 16), np.uint32)
+        prims = np.zeros((max(M, 0), 16), np.uint32)
+        codes = np.zeros(max(M, 0), np.uint64)
+        order = np.zeros(max(M, 0), np.uint32)
+        ptr = lambda a: a.ctypes.data_as(C.c_void_p) if a.size else None  # noqa: E731
+        _check(lib().gs_bvh_export(self._h, ptr(nodes), ptr(prims), ptr(codes), ptr(order)))
+        return {"nodes": nodes, "prims": prims, "codes": codes, "order": order}
+
+    def free(self):
+        if self._h is not None and _lib is not None:
+            lib().gs_bvh_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_bvh(g: Gaussians, stream=None) -> Bvh:
+    """``gs_build_bvh``: hierarchy over the Gaussians' bounding boxes."""
+    h = C.c_void_p()
+    gs = g.struct()
+    _check(lib().gs_build_bvh(C.byref(gs), C.byref(h), _stream_handle(stream)))
+    return Bvh(h, g.M)
+
+
+# ---------------------------------------------------------------- tracing
+
+
+def trace_stochastic(bvh: Bvh, g: Gaussians, cam, seed=0, spp=1, n_hits=1, t_min=0.0,
+                     t_max=float("inf"), bg=(0.0, 0.0, 0.0), stack_depth=0, stream_tag=0,
+                     want_hits=False, counters=None, out=None, stream=None):
+    """``gs_trace_stochastic``: render one pinhole view.
+
+    Returns ``rgb`` [H, W, 3] float32 (and ``hit_id``, ``hit_t`` of shape
+    [spp, n_hits, H, W] when ``want_hits``), all on the current CUDA device."""
+    cam = cam if isinstance(cam, Camera) else Camera.of(cam)
+    H, W = int(cam.height), int(cam.width)
+    dev = g.means.device
+    rgb = out if out is not None else torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    hit_id = hit_t = None
+    if want_hits:
+        hit_id = torch.empty((spp, n_hits, H, W), dtype=torch.int32, device=dev)
+        hit_t = torch.empty((spp, n_hits, H, W), dtype=torch.float32, device=dev)
+    gs = g.struct()
+    cs = cam.struct()
+    ps = _params(seed, spp, n_hits, t_min, t_max, bg, stack_depth, stream_tag, counters)
+    _check(lib().gs_trace_stochastic(
+        bvh.handle, C.byref(gs), C.byref(cs), C.byref(ps), C.c_void_p(rgb.data_ptr()),
+        None if hit_id is None else C.c_void_p(hit_id.data_ptr()),
+        None if hit_t is None else C.c_void_p(hit_t.data_ptr()), _stream_handle(stream)))
+    if want_hits:
+        return rgb, hit_id, hit_t
+    return rgb
+
+
+def render(g: Gaussians, cam, stream=None, **kw):
+    """Build a hierarchy and trace one view (convenience for one-off use)."""
+    bvh = build_bvh(g, stream)
+    try:
+        res = trace_stochastic(bvh, g, cam, stream=stream, **kw)
+        bvh.sync_status(stream)
+        return res
+    finally:
+        bvh.free()

@@ -1,0 +1,278 @@
+// api.cu -- the C ABI of include/gsrt.h: argument validation, handle
+// lifecycle, status reporting. Kernels live in build.cu and trace.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "gsrt_internal.cuh"
+
+namespace gsrt {
+
+static thread_local char g_last_error[512] = "";
+
+gs_status fail(gs_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+gs_status cuda_fail(cudaError_t e, const char *what) {
+    gs_status s = (e == cudaErrorMemoryAllocation) ? GS_ERR_OOM
+                  : (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) ? GS_ERR_NO_DEVICE
+                                                                                  : GS_ERR_CUDA;
+    return fail(s, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static gs_status check_device() {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return fail(GS_ERR_NO_DEVICE, "no CUDA device available");
+    }
+    return GS_OK;
+}
+
+// Host-only checks of a parameter struct (no CUDA call).
+static gs_status check_gaussians_host(const gs_gaussians *g, bool need_sh) {
+    if (!g) return fail(GS_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->M < 0 || g->M >= (int64_t)0x7fffffff)
+        return fail(GS_ERR_INVALID_ARG, "M=%lld out of range [0, 2^31-1)", (long long)g->M);
+    if (g->M > 0) {
+        if (!g->means || !g->log_scales || !g->quats || !g->opacity_logits)
+            return fail(GS_ERR_INVALID_ARG, "a Gaussian parameter pointer is NULL");
+        if (need_sh && !g->sh) return fail(GS_ERR_INVALID_ARG, "sh is NULL");
+    }
+    if (g->sh_degree < 0 || g->sh_degree > 3)
+        return fail(GS_ERR_INVALID_ARG, "sh_degree=%d not in 0..3", g->sh_degree);
+    if (g->sh_dtype != GS_SH_F32 && g->sh_dtype != GS_SH_F16 && g->sh_dtype != GS_SH_BF16)
+        return fail(GS_ERR_INVALID_ARG, "sh_dtype=%d unknown", g->sh_dtype);
+    if (need_sh && g->M > 0 && g->sh_dtype == GS_SH_F32 && !aligned16(g->sh))
+        return fail(GS_ERR_INVALID_ARG, "float32 sh must be 16-byte aligned");
+    return GS_OK;
+}
+
+static gs_status check_gaussians_device(const gs_gaussians *g, bool need_sh) {
+    if (g->M == 0) return GS_OK;
+    const void *ptrs[5] = {g->means, g->log_scales, g->quats, g->opacity_logits, g->sh};
+    const char *names[5] = {"means", "log_scales", "quats", "opacity_logits", "sh"};
+    for (int i = 0; i < (need_sh ? 5 : 4); ++i)
+        if (!is_device_ptr(ptrs[i]))
+            return fail(GS_ERR_INVALID_ARG, "%s is not a device pointer", names[i]);
+    return GS_OK;
+}
+
+static void release(gs_bvh *b) {
+    if (!b) return;
+    void *bufs[] = {b->nodes, b->prims, b->status, b->codes[0], b->codes[1], b->vals[0],
+                    b->vals[1], b->parent, b->arrive, b->aabb, b->bounds, b->hist};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    free(b);
+}
+
+}  // namespace gsrt
+
+using namespace gsrt;
+
+extern "C" {
+
+const char *gs_status_string(gs_status s) {
+    switch (s) {
+        case GS_OK: return "ok";
+        case GS_ERR_INVALID_ARG: return "invalid argument";
+        case GS_ERR_CUDA: return "CUDA error";
+        case GS_ERR_OOM: return "out of device memory";
+        case GS_ERR_STACK_OVERFLOW: return "traversal stack overflow";
+        case GS_ERR_STEP_LIMIT: return "traversal step limit exceeded";
+        case GS_ERR_NONFINITE: return "non-finite Gaussian parameter";
+        case GS_ERR_NO_DEVICE: return "no CUDA device";
+    }
+    return "unknown status";
+}
+
+const char *gs_last_error(void) { return g_last_error; }
+
+gs_status gs_build_bvh(const gs_gaussians *g, gs_bvh **out, void *stream) {
+    if (!out) return fail(GS_ERR_INVALID_ARG, "out is NULL");
+    gs_status st = check_gaussians_host(g, false);
+    if (st != GS_OK) return st;
+    if ((st = check_device()) != GS_OK) return st;
+    if ((st = check_gaussians_device(g, false)) != GS_OK) return st;
+    gs_bvh *b = (gs_bvh *)calloc(1, sizeof(gs_bvh));
+    if (!b) return fail(GS_ERR_OOM, "host allocation failed");
+    cudaGetDevice(&b->device);
+    const int64_t M = g->M;
+    const int64_t cap = M > 0 ? M : 0;
+    const int64_t nn = M > 1 ? M - 1 : 1;
+    const int64_t tiles = radix_tiles(cap > 0 ? cap : 1);
+    struct Req { void **p; size_t bytes; } reqs[] = {
+        {(void **)&b->status, 16},
+        {(void **)&b->nodes, (size_t)nn * sizeof(Node)},
+        {(void **)&b->prims, (size_t)(cap > 0 ? cap : 1) * sizeof(PrimRec)},
+        {(void **)&b->codes[0], (size_t)(cap > 0 ? cap : 1) * 8},
+        {(void **)&b->codes[1], (size_t)(cap > 0 ? cap : 1) * 8},
+        {(void **)&b->vals[0], (size_t)(cap > 0 ? cap : 1) * 4},
+        {(void **)&b->vals[1], (size_t)(cap > 0 ? cap : 1) * 4},
+        {(void **)&b->parent, (size_t)(2 * cap + 2) * 4},
+        {(void **)&b->arrive, (size_t)(cap > 0 ? cap : 1) * 4},
+        {(void **)&b->aabb, (size_t)(cap > 0 ? cap : 1) * 24},
+        {(void **)&b->bounds, 64},
+        {(void **)&b->hist, (size_t)256 * tiles * 4},
+    };
+    int64_t total = 0;
+    for (auto &r : reqs) {
+        cudaError_t e = cudaMalloc(r.p, r.bytes);
+        if (e != cudaSuccess) {
+            release(b);
+            return cuda_fail(e, "cudaMalloc");
+        }
+        total += (int64_t)r.bytes;
+    }
+    b->capacity = cap;
+    b->hist_len = 256 * tiles;
+    b->device_bytes = total;
+    cudaError_t e = cudaMemsetAsync(b->status, 0, 16, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        release(b);
+        return cuda_fail(e, "memset status");
+    }
+    st = build_into(b, g, (cudaStream_t)stream);
+    if (st != GS_OK) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        release(b);
+        return st;
+    }
+    *out = b;
+    return GS_OK;
+}
+
+gs_status gs_bvh_rebuild(gs_bvh *b, const gs_gaussians *g, void *stream) {
+    if (!b) return fail(GS_ERR_INVALID_ARG, "bvh is NULL");
+    gs_status st = check_gaussians_host(g, false);
+    if (st != GS_OK) return st;
+    if (g->M > b->capacity)
+        return fail(GS_ERR_INVALID_ARG, "M=%lld exceeds capacity %lld", (long long)g->M,
+                    (long long)b->capacity);
+    if ((st = check_gaussians_device(g, false)) != GS_OK) return st;
+    return build_into(b, g, (cudaStream_t)stream);
+}
+
+gs_status gs_bvh_free(gs_bvh *b) {
+    if (!b) return GS_OK;
+    cudaDeviceSynchronize();
+    release(b);
+    return GS_OK;
+}
+
+gs_status gs_bvh_get_info(const gs_bvh *b, gs_bvh_info *info) {
+    if (!b || !info) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+    info->M = b->M;
+    info->n_nodes = b->n_nodes;
+    info->capacity = b->capacity;
+    info->device_bytes = b->device_bytes;
+    info->node_bytes = (int32_t)sizeof(Node);
+    info->prim_bytes = (int32_t)sizeof(PrimRec);
+    return GS_OK;
+}
+
+gs_status gs_bvh_sync_status(gs_bvh *b, void *stream) {
+    if (!b) return fail(GS_ERR_INVALID_ARG, "bvh is NULL");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    uint32_t word = 0;
+    if ((e = cudaMemcpy(&word, b->status, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "read status");
+    if (word) {
+        if ((e = cudaMemset(b->status, 0, 4)) != cudaSuccess) return cuda_fail(e, "clear status");
+    }
+    if (word & kErrNonfinite) return fail(GS_ERR_NONFINITE, "non-finite Gaussian parameter(s)");
+    if (word & kErrStack) return fail(GS_ERR_STACK_OVERFLOW, "a ray overflowed its stack");
+    if (word & kErrSteps) return fail(GS_ERR_STEP_LIMIT, "a ray exceeded the step limit");
+    return GS_OK;
+}
+
+gs_status gs_bvh_export(const gs_bvh *b, void *nodes_out, void *prims_out, uint64_t *codes_out,
+                        uint32_t *order_out) {
+    if (!b) return fail(GS_ERR_INVALID_ARG, "bvh is NULL");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    if (b->M == 0) return GS_OK;
+    if (nodes_out &&
+        (e = cudaMemcpy(nodes_out, b->nodes, (size_t)b->n_nodes * sizeof(Node),
+                        cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "copy nodes");
+    if (prims_out &&
+        (e = cudaMemcpy(prims_out, b->prims, (size_t)b->M * sizeof(PrimRec),
+                        cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "copy prims");
+    if (codes_out &&
+        (e = cudaMemcpy(codes_out, b->codes[b->final_buf], (size_t)b->M * 8,
+                        cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "copy codes");
+    if (order_out &&
+        (e = cudaMemcpy(order_out, b->vals[b->final_buf], (size_t)b->M * 4,
+                        cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "copy order");
+    return GS_OK;
+}
+
+gs_status gs_trace_stochastic(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
+                              const gs_trace_params *p, float *rgb_out, int32_t *hit_id_out,
+                              float *hit_t_out, void *stream) {
+    if (!b) return fail(GS_ERR_INVALID_ARG, "bvh is NULL");
+    gs_status st = check_gaussians_host(g, true);
+    if (st != GS_OK) return st;
+    if (g->M != b->M)
+        return fail(GS_ERR_INVALID_ARG, "gaussians M=%lld differs from the hierarchy's M=%lld",
+                    (long long)g->M, (long long)b->M);
+    if (!cam || !p || !rgb_out) return fail(GS_ERR_INVALID_ARG, "cam, params or rgb_out is NULL");
+    if (cam->width < 1 || cam->height < 1 || cam->width > 65536 || cam->height > 65536)
+        return fail(GS_ERR_INVALID_ARG, "image size %dx%d out of range", cam->width, cam->height);
+    if ((uint64_t)cam->ray_id_offset + (uint64_t)cam->width * (uint64_t)cam->height >
+        0x100000000ull)
+        return fail(GS_ERR_INVALID_ARG, "ray ids exceed 32 bits");
+    if (!(cam->fov_y_deg > 0.0f && cam->fov_y_deg < 180.0f))
+        return fail(GS_ERR_INVALID_ARG, "fov_y_deg=%g not in (0, 180)", (double)cam->fov_y_deg);
+    for (int i = 0; i < 3; ++i)
+        if (!isfinite(cam->eye[i]) || !isfinite(cam->look_at[i]) || !isfinite(cam->up[i]))
+            return fail(GS_ERR_INVALID_ARG, "camera vectors must be finite");
+    if (p->spp < 1 || p->spp > (1 << 20)) return fail(GS_ERR_INVALID_ARG, "spp=%d out of range", p->spp);
+    if (p->n_hits != 1 && p->n_hits != 2 && p->n_hits != 4 && p->n_hits != 8)
+        return fail(GS_ERR_INVALID_ARG, "n_hits=%d must be 1, 2, 4 or 8", p->n_hits);
+    if ((int64_t)p->spp * p->n_hits > (1ll << 30))
+        return fail(GS_ERR_INVALID_ARG, "spp * n_hits too large");
+    if (p->stack_depth < 0 || p->stack_depth > kMaxStack)
+        return fail(GS_ERR_INVALID_ARG, "stack_depth=%d not in 0..%d", p->stack_depth, kMaxStack);
+    if (p->depth_mode != 0) return fail(GS_ERR_INVALID_ARG, "depth_mode=%d unsupported", p->depth_mode);
+    if (isnan(p->t_min) || isnan(p->t_max) || !(p->t_min < p->t_max))
+        return fail(GS_ERR_INVALID_ARG, "need t_min < t_max");
+    if ((hit_id_out == nullptr) != (hit_t_out == nullptr))
+        return fail(GS_ERR_INVALID_ARG, "hit_id_out and hit_t_out go together");
+    if ((st = check_device()) != GS_OK) return st;
+    if ((st = check_gaussians_device(g, true)) != GS_OK) return st;
+    if (!is_device_ptr(rgb_out)) return fail(GS_ERR_INVALID_ARG, "rgb_out is not a device pointer");
+    if (hit_id_out && (!is_device_ptr(hit_id_out) || !is_device_ptr(hit_t_out)))
+        return fail(GS_ERR_INVALID_ARG, "hit outputs must be device pointers");
+    if (p->counters && !is_device_ptr(p->counters))
+        return fail(GS_ERR_INVALID_ARG, "counters is not a device pointer");
+    return launch_trace(b, g, cam, p, rgb_out, hit_id_out, hit_t_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

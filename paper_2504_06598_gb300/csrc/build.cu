@@ -1,0 +1,427 @@
+// build.cu -- hierarchy construction over the Gaussians' bounding boxes
+// (Sec. 3.2 builds a BVH over the boxes of Eq. 2; the paper delegates it to
+// Embree/OptiX, here it is a linear BVH built on the GPU):
+//   k_preprocess  box of each Gaussian's bounding ellipsoid + scene bounds
+//   k_morton      63-bit Morton code of each mean in the scene bounds
+//   radix sort    stable LSD sort of (code, id), 8 passes of 8 bits
+//   k_karras      binary radix tree over the sorted codes (Karras 2012),
+//                 equal codes split by position
+//   k_leaves      per-Gaussian record in tree order, then bottom-up box
+//                 refit with one arrival counter per node
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "gsrt_internal.cuh"
+
+namespace gsrt {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kScanThreads = 1024;
+
+// Order-preserving map float -> uint32 (for atomicMin / atomicMax).
+__device__ __forceinline__ unsigned int f2ord(float f) {
+    unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(unsigned int u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+struct Activated {
+    float mu[3];
+    float opacity;
+    float R[9];  // R_q, local to world, row-major
+    float inv_s[3];
+    float s[3];
+    bool finite;
+};
+
+// Eq. 1 activation in float32: normalised quaternion -> rotation,
+// exp of log-scales, sigmoid of the opacity logit.
+__device__ __forceinline__ Activated activate(const float *means, const float *log_scales,
+                                              const float *quats, const float *logits,
+                                              int64_t g) {
+    Activated a;
+    float qw = quats[4 * g + 0], qx = quats[4 * g + 1], qy = quats[4 * g + 2],
+          qz = quats[4 * g + 3];
+    float n2 = qw * qw + qx * qx + qy * qy + qz * qz;
+    float inv = 1.0f / sqrtf(n2);
+    qw *= inv; qx *= inv; qy *= inv; qz *= inv;
+    a.R[0] = 1.0f - 2.0f * (qy * qy + qz * qz);
+    a.R[1] = 2.0f * (qx * qy - qw * qz);
+    a.R[2] = 2.0f * (qx * qz + qw * qy);
+    a.R[3] = 2.0f * (qx * qy + qw * qz);
+    a.R[4] = 1.0f - 2.0f * (qx * qx + qz * qz);
+    a.R[5] = 2.0f * (qy * qz - qw * qx);
+    a.R[6] = 2.0f * (qx * qz - qw * qy);
+    a.R[7] = 2.0f * (qy * qz + qw * qx);
+    a.R[8] = 1.0f - 2.0f * (qx * qx + qy * qy);
+    bool fin = isfinite(n2) && n2 > 0.0f;
+    for (int k = 0; k < 3; ++k) {
+        float ls = log_scales[3 * g + k];
+        a.mu[k] = means[3 * g + k];
+        a.s[k] = expf(ls);
+        a.inv_s[k] = expf(-ls);
+        fin = fin && isfinite(ls) && isfinite(a.mu[k]) && a.s[k] > 0.0f && isfinite(a.s[k]) &&
+              isfinite(a.inv_s[k]);
+    }
+    float lg = logits[g];
+    fin = fin && isfinite(lg);
+    a.opacity = 1.0f / (1.0f + expf(-lg));
+    a.finite = fin;
+    return a;
+}
+
+// Box of the ellipsoid |S^-1 R_q^T (x - mu)| <= s: half extent along world
+// axis i is s * sqrt(sum_k R_ik^2 s_k^2). Padded outward (relative 2^-10 of
+// the extent plus 2^-18 of the coordinate magnitude) so that float32
+// rounding in the ellipsoid and slab tests never loses a valid hit.
+__device__ __forceinline__ void ellipsoid_box(const Activated &a, float box[6]) {
+    const float s_cut = 2.8284271247461903f;
+    for (int i = 0; i < 3; ++i) {
+        float v = 0.0f;
+        for (int k = 0; k < 3; ++k) {
+            float r = a.R[3 * i + k] * a.s[k];
+            v = fmaf(r, r, v);
+        }
+        float h = s_cut * sqrtf(v);
+        float pad = h * 0x1p-10f + (fabsf(a.mu[i]) + h) * 0x1p-18f;
+        box[i] = a.mu[i] - (h + pad);
+        box[3 + i] = a.mu[i] + (h + pad);
+    }
+}
+
+__global__ void k_preprocess(int64_t M, const float *__restrict__ means,
+                             const float *__restrict__ log_scales, const float *__restrict__ quats,
+                             const float *__restrict__ logits, float *__restrict__ aabb,
+                             unsigned int *__restrict__ bounds, uint32_t *__restrict__ status) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (g < M) {
+        Activated a = activate(means, log_scales, quats, logits, g);
+        float box[6];
+        if (a.finite) {
+            ellipsoid_box(a, box);
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = a.mu[k];
+                hi[k] = a.mu[k];
+            }
+        } else {
+            // A non-finite Gaussian gets an empty box: it is never hit.
+            for (int k = 0; k < 3; ++k) {
+                box[k] = NAN;
+                box[3 + k] = NAN;
+            }
+            atomicOr(status, kErrNonfinite);
+        }
+        for (int k = 0; k < 6; ++k) aabb[6 * g + k] = box[k];
+    }
+    // warp reduction of the finite means, then one atomic per warp
+    for (int k = 0; k < 3; ++k) {
+        for (int off = 16; off > 0; off >>= 1) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], off));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], off));
+        }
+    }
+    if ((threadIdx.x & 31) == 0 && lo[0] <= hi[0]) {
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&bounds[k], f2ord(lo[k]));
+            atomicMax(&bounds[3 + k], f2ord(hi[k]));
+        }
+    }
+}
+
+// Spread the low 21 bits of v to every third bit of a 64-bit word.
+__device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__global__ void k_morton(int64_t M, const float *__restrict__ means,
+                         const unsigned int *__restrict__ bounds,
+                         unsigned long long *__restrict__ codes, uint32_t *__restrict__ vals) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= M) return;
+    unsigned long long q[3];
+    for (int k = 0; k < 3; ++k) {
+        float lo = ord2f(bounds[k]), hi = ord2f(bounds[3 + k]);
+        float ext = hi - lo;
+        float x = means[3 * g + k];
+        float u = (ext > 0.0f) ? (x - lo) / ext : 0.0f;
+        u = fminf(fmaxf(u, 0.0f), 1.0f);  // NaN -> 0
+        q[k] = (unsigned long long)(u * 2097151.0f);
+    }
+    codes[g] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+    vals[g] = (uint32_t)g;
+}
+
+// ---------------------------------------------------------------- radix sort
+
+__global__ void __launch_bounds__(kSortThreads)
+    k_radix_hist(int64_t n, const unsigned long long *__restrict__ keys, int shift,
+                 uint32_t *__restrict__ hist, int64_t tiles) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortItems; ++r) {
+        int64_t i = base + r * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of len entries by one block of kScanThreads threads.
+__global__ void __launch_bounds__(kScanThreads) k_radix_scan(uint32_t *__restrict__ a, int64_t len) {
+    __shared__ uint32_t warp_sums[kScanThreads / 32];
+    int64_t chunk = (len + kScanThreads - 1) / kScanThreads;
+    int64_t b = threadIdx.x * chunk, e = min(b + chunk, len);
+    uint32_t sum = 0;
+    for (int64_t i = b; i < e; ++i) sum += a[i];
+    // block-wide exclusive scan of the per-thread sums
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = sum;
+    for (int off = 1; off < 32; off <<= 1) {
+        uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = warp_sums[lane];
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t v = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += v;
+        }
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = incl - sum + (warp > 0 ? warp_sums[warp - 1] : 0u);
+    for (int64_t i = b; i < e; ++i) {
+        uint32_t v = a[i];
+        a[i] = run;
+        run += v;
+    }
+}
+
+// Stable scatter: keys of a tile are ranked in input order, round by round
+// (256 keys per round), with warp-level digit matching and a per-digit
+// prefix over the warps of the block.
+__global__ void __launch_bounds__(kSortThreads)
+    k_radix_scatter(int64_t n, const unsigned long long *__restrict__ kin,
+                    const uint32_t *__restrict__ vin, unsigned long long *__restrict__ kout,
+                    uint32_t *__restrict__ vout, int shift, const uint32_t *__restrict__ offs,
+                    int64_t tiles) {
+    constexpr int W = kSortThreads / 32;
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wcount[W][256];
+    __shared__ uint32_t pref[W][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    base[tid] = offs[(int64_t)tid * tiles + blockIdx.x];
+    for (int w = 0; w < W; ++w) wcount[w][tid] = 0;
+    __syncthreads();
+    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortItems; ++r) {
+        int64_t i = tile0 + r * kSortThreads + tid;
+        bool valid = i < n;
+        unsigned long long key = valid ? kin[i] : 0ull;
+        uint32_t val = valid ? vin[i] : 0u;
+        uint32_t digit = valid ? ((uint32_t)(key >> shift) & 255u) : (256u + lane);
+        uint32_t peers = __match_any_sync(0xffffffffu, digit);
+        uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) wcount[warp][digit] = __popc(peers);
+        __syncthreads();
+        uint32_t run = base[tid];
+        for (int w = 0; w < W; ++w) {
+            uint32_t c = wcount[w][tid];
+            pref[w][tid] = run;
+            wcount[w][tid] = 0;
+            run += c;
+        }
+        base[tid] = run;
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = pref[warp][digit] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- hierarchy
+
+// Common-prefix length of sorted keys i and j, extended by the index bits
+// when the codes are equal; -1 outside [0, n).
+__device__ __forceinline__ int delta(const unsigned long long *__restrict__ codes, int64_t n,
+                                     int64_t i, int64_t j) {
+    if (j < 0 || j >= n) return -1;
+    unsigned long long a = codes[i], b = codes[j];
+    if (a == b) return 64 + __clz((uint32_t)(i ^ j));
+    return __clzll(a ^ b);
+}
+
+__global__ void k_karras(int64_t n, const unsigned long long *__restrict__ codes,
+                         Node *__restrict__ nodes, uint32_t *__restrict__ parent_int,
+                         uint32_t *__restrict__ parent_leaf) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (delta(codes, n, i, i + 1) - delta(codes, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = delta(codes, n, i, i - d);
+    int64_t lmax = 2;
+    while (delta(codes, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int64_t l = 0;
+    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(codes, n, i, i + (l + t) * d) > dmin) l += t;
+    int64_t j = i + l * d;
+    int dnode = delta(codes, n, i, j);
+    int64_t s = 0;
+    for (int64_t div = 2;; div <<= 1) {
+        int64_t t = (l + div - 1) / div;
+        if (delta(codes, n, i, i + (s + t) * d) > dnode) s += t;
+        if (t <= 1) break;
+    }
+    int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+    int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    uint32_t left = (lo == gamma) ? (kLeafBit | (uint32_t)gamma) : (uint32_t)gamma;
+    uint32_t right = (hi == gamma + 1) ? (kLeafBit | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
+    Node &nd = nodes[i];
+    nd.child[0] = left;
+    nd.child[1] = right;
+    nd.reserved[0] = 0;
+    nd.reserved[1] = 0;
+    if (left & kLeafBit) parent_leaf[gamma] = (uint32_t)i; else parent_int[gamma] = (uint32_t)i;
+    if (right & kLeafBit) parent_leaf[gamma + 1] = (uint32_t)i; else parent_int[gamma + 1] = (uint32_t)i;
+}
+
+__device__ __forceinline__ void write_record(PrimRec *__restrict__ prims, int64_t i, uint32_t g,
+                                             const Activated &a) {
+    PrimRec r;
+    for (int k = 0; k < 3; ++k) r.mu[k] = a.mu[k];
+    r.opacity = a.opacity;
+    // M = S^-1 R_q^T: row k is column k of R_q divided by s_k
+    for (int k = 0; k < 3; ++k)
+        for (int j = 0; j < 3; ++j) r.m[3 * k + j] = a.R[3 * j + k] * a.inv_s[k];
+    if (!a.finite)
+        for (int k = 0; k < 9; ++k) r.m[k] = NAN;
+    r.gid = g;
+    r.pad[0] = 0.0f;
+    r.pad[1] = 0.0f;
+    float4 *dst = reinterpret_cast<float4 *>(prims + i);
+    const float4 *src = reinterpret_cast<const float4 *>(&r);
+    for (int k = 0; k < 4; ++k) dst[k] = src[k];
+}
+
+// One thread per leaf (tree position i): write the Gaussian record, then
+// carry boxes towards the root; the second thread to reach a node merges
+// both child boxes and continues.
+__global__ void k_leaves(int64_t n, const uint32_t *__restrict__ order,
+                         const float *__restrict__ means, const float *__restrict__ log_scales,
+                         const float *__restrict__ quats, const float *__restrict__ logits,
+                         const float *__restrict__ aabb, PrimRec *__restrict__ prims,
+                         Node *__restrict__ nodes, const uint32_t *__restrict__ parent_int,
+                         const uint32_t *__restrict__ parent_leaf, uint32_t *__restrict__ arrive) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t g = order[i];
+    Activated a = activate(means, log_scales, quats, logits, g);
+    write_record(prims, i, g, a);
+    float box[6];
+    for (int k = 0; k < 6; ++k) box[k] = aabb[6 * (int64_t)g + k];
+    uint32_t ref = kLeafBit | (uint32_t)i;
+    uint32_t p = parent_leaf[i];
+    for (int guard = 0; guard < 4096; ++guard) {
+        Node *nd = nodes + p;
+        int side = (__ldcg(&nd->child[0]) == ref) ? 0 : 1;
+        for (int k = 0; k < 6; ++k) __stcg(&nd->box[side][k], box[k]);
+        __threadfence();
+        if (atomicAdd(&arrive[p], 1u) == 0u) return;
+        __threadfence();
+        for (int k = 0; k < 3; ++k) {
+            box[k] = fminf(box[k], __ldcg(&nd->box[1 - side][k]));
+            box[3 + k] = fmaxf(box[3 + k], __ldcg(&nd->box[1 - side][3 + k]));
+        }
+        if (p == 0) return;
+        ref = p;
+        p = parent_int[p];
+    }
+}
+
+// M == 1: a root whose two children are the same leaf. Draws are keyed by
+// (ray, Gaussian, sample), so testing the leaf twice gives the same answer.
+__global__ void k_single(const uint32_t *__restrict__ order, const float *__restrict__ means,
+                         const float *__restrict__ log_scales, const float *__restrict__ quats,
+                         const float *__restrict__ logits, const float *__restrict__ aabb,
+                         PrimRec *__restrict__ prims, Node *__restrict__ nodes) {
+    uint32_t g = order[0];
+    Activated a = activate(means, log_scales, quats, logits, g);
+    write_record(prims, 0, g, a);
+    Node nd;
+    for (int s = 0; s < 2; ++s) {
+        for (int k = 0; k < 6; ++k) nd.box[s][k] = aabb[6 * (int64_t)g + k];
+        nd.child[s] = kLeafBit;
+    }
+    nd.reserved[0] = nd.reserved[1] = 0;
+    nodes[0] = nd;
+}
+
+inline unsigned grid_for(int64_t n, int threads) {
+    return (unsigned)((n + threads - 1) / threads);
+}
+
+}  // namespace
+
+int64_t radix_tiles(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+
+gs_status build_into(gs_bvh *b, const gs_gaussians *g, cudaStream_t s) {
+    const int64_t M = g->M;
+    b->M = M;
+    b->n_nodes = M == 0 ? 0 : (M == 1 ? 1 : M - 1);
+    if (M == 0) return GS_OK;
+    cudaError_t e;
+    // bounds: mins start at the largest ordered value, maxes at the smallest
+    if ((e = cudaMemsetAsync(b->bounds, 0xff, 3 * sizeof(unsigned int), s)) != cudaSuccess)
+        return cuda_fail(e, "memset bounds");
+    if ((e = cudaMemsetAsync(b->bounds + 3, 0, 3 * sizeof(unsigned int), s)) != cudaSuccess)
+        return cuda_fail(e, "memset bounds");
+    k_preprocess<<<grid_for(M, 256), 256, 0, s>>>(M, g->means, g->log_scales, g->quats,
+                                                   g->opacity_logits, b->aabb, b->bounds, b->status);
+    k_morton<<<grid_for(M, 256), 256, 0, s>>>(M, g->means, b->bounds, b->codes[0], b->vals[0]);
+    const int64_t tiles = radix_tiles(M);
+    int cur = 0;
+    for (int shift = 0; shift < 64; shift += 8) {
+        k_radix_hist<<<(unsigned)tiles, kSortThreads, 0, s>>>(M, b->codes[cur], shift, b->hist, tiles);
+        k_radix_scan<<<1, kScanThreads, 0, s>>>(b->hist, 256 * tiles);
+        k_radix_scatter<<<(unsigned)tiles, kSortThreads, 0, s>>>(
+            M, b->codes[cur], b->vals[cur], b->codes[1 - cur], b->vals[1 - cur], shift, b->hist,
+            tiles);
+        cur = 1 - cur;
+    }
+    b->final_buf = cur;
+    const uint32_t *order = b->vals[cur];
+    if (M == 1) {
+        k_single<<<1, 1, 0, s>>>(order, g->means, g->log_scales, g->quats, g->opacity_logits,
+                                 b->aabb, b->prims, b->nodes);
+    } else {
+        uint32_t *parent_int = b->parent, *parent_leaf = b->parent + M;
+        k_karras<<<grid_for(M - 1, 256), 256, 0, s>>>(M, b->codes[cur], b->nodes, parent_int,
+                                                       parent_leaf);
+        if ((e = cudaMemsetAsync(b->arrive, 0, (size_t)M * sizeof(uint32_t), s)) != cudaSuccess)
+            return cuda_fail(e, "memset arrive");
+        k_leaves<<<grid_for(M, 256), 256, 0, s>>>(M, order, g->means, g->log_scales, g->quats,
+                                                   g->opacity_logits, b->aabb, b->prims, b->nodes,
+                                                   parent_int, parent_leaf, b->arrive);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "build launch");
+    return GS_OK;
+}
+
+}  // namespace gsrt

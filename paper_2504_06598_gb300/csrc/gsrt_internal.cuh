@@ -1,0 +1,92 @@
+// gsrt_internal.cuh -- device records, helpers and launch declarations shared
+// by the build, trace and API translation units of the GB300 library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gsrt.h"
+
+namespace gsrt {
+
+// --------------------------------------------------------------------------
+// Records in device memory
+// --------------------------------------------------------------------------
+
+// One Gaussian, in hierarchy (Morton) order, 64 bytes = four 16-byte loads.
+// m[] is the local transform M = S^-1 R_q^T (row-major): for a world vector
+// v, |M v|^2 is the Mahalanobis form of Eq. 1, so the bounding ellipsoid of
+// Eq. 2 is |M (x - mu)| <= s.
+struct __align__(16) PrimRec {
+    float mu[3];
+    float opacity;
+    float m[9];
+    uint32_t gid;
+    float pad[2];
+};
+static_assert(sizeof(PrimRec) == 64, "PrimRec must be 64 bytes");
+
+// Binary node, 64 bytes: boxes of both children and their references.
+struct __align__(16) Node {
+    float box[2][6];  // {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z} left, right
+    uint32_t child[2];
+    uint32_t reserved[2];
+};
+static_assert(sizeof(Node) == 64, "Node must be 64 bytes");
+
+constexpr uint32_t kLeafBit = 0x80000000u;
+constexpr int kMaxStack = 64;
+constexpr uint32_t kStepLimit = 1u << 22;  // node visits per ray and pass
+
+// Device status word bits.
+constexpr uint32_t kErrStack = 1u << 0;
+constexpr uint32_t kErrSteps = 1u << 1;
+constexpr uint32_t kErrNonfinite = 1u << 2;
+
+// s^2 of Eq. 2 with s = 2 sqrt(2).
+constexpr float kS2 = 8.0f;
+
+}  // namespace gsrt
+
+// --------------------------------------------------------------------------
+// Handle (host side)
+// --------------------------------------------------------------------------
+struct gs_bvh {
+    int device;
+    int64_t M;
+    int64_t capacity;
+    int64_t n_nodes;
+    int64_t device_bytes;
+    // persistent outputs
+    gsrt::Node *nodes;
+    gsrt::PrimRec *prims;
+    uint32_t *status;  // device status word
+    // build scratch (kept for rebuilds)
+    unsigned long long *codes[2];
+    uint32_t *vals[2];
+    uint32_t *parent;   // [2M]: parents of internal nodes (0..M-2) then leaves
+    uint32_t *arrive;   // [M] refit arrival counters
+    float *aabb;        // [M][6] in Gaussian-id order
+    unsigned int *bounds;  // [6] ordered-int scene bounds of the means
+    uint32_t *hist;     // radix histograms [256 * tiles]
+    int64_t hist_len;
+    int final_buf;      // which of codes/vals holds the sorted result
+};
+
+namespace gsrt {
+
+// Host-side helpers (api.cu)
+gs_status fail(gs_status s, const char *fmt, ...);
+gs_status cuda_fail(cudaError_t e, const char *what);
+bool is_device_ptr(const void *p);
+
+// Build pipeline (build.cu)
+gs_status build_into(gs_bvh *b, const gs_gaussians *g, cudaStream_t s);
+int64_t radix_tiles(int64_t n);
+
+// Trace (trace.cu)
+gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
+                       const gs_trace_params *p, float *rgb, int32_t *hit_id, float *hit_t,
+                       cudaStream_t s);
+
+}  // namespace gsrt

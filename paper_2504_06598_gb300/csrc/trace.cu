@@ -1,0 +1,495 @@
+// trace.cu -- stochastic ray tracing of transparent Gaussians on sm_103a.
+//
+// One thread per pixel. Each pass is one traversal of the hierarchy
+// (Sec. 3.2) keeping N closest accepted intersections (Sec. 3.5). At every
+// leaf the intersection routine of Alg. 1 runs:
+//   t    mean of the 1D Gaussian along the ray (Sec. 3.1)
+//   cull if t <= t_min or t is not before the slot's hit, or if the mean
+//        lies outside the bounding ellipsoid (Eq. 2: q > s^2 = 8)
+//   alpha = opacity * exp(-q/2), q the minimum of the Mahalanobis form
+//   accept iff xi < alpha (Eq. 4, Fig. 2), replacing the slot (Eq. 6) and
+//        clipping the traversal range to the farthest slot.
+// After the traversal each slot is shaded once (SH colour, Sec. 3.2) or gets
+// the background, and the pixel accumulates the mean of Eq. 7.
+//
+// Float32 formulation of the 1D Gaussian. With o the ray origin, d the unit
+// direction, mu the mean and M = S^-1 R_q^T:
+//   o - mu = h + l exactly (h rounded, l its rounding error),
+//   tc = -(h . d) puts the base point P = o + tc d near the mean,
+//   w = P - mu = fma(tc, d, h) + l is accurate to the rounding of its own
+//       (small) magnitude, whatever rounding tc carries, because q does not
+//       depend on which point of the ray is used as base,
+//   tau = -(Mw . Md) / |Md|^2 is the 1D mean relative to P,
+//   w2 = w + tau d, q = |M w2|^2 - (M w2 . Md)^2 / |Md|^2.
+// The depth is t = tc + tau; depths are compared through (tc, tau) pairs so
+// that two nearby hits are ordered to the accuracy of tau, not of t.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "gsrt_internal.cuh"
+
+namespace gsrt {
+namespace {
+
+constexpr int kTileW = 16, kTileH = 8, kThreads = 128;
+
+struct TraceArgs {
+    const Node *nodes;
+    const PrimRec *prims;
+    const void *sh;
+    int64_t n_nodes;
+    int sh_degree;
+    int sh_dtype;
+    int width, height;
+    uint32_t ray_id_offset;
+    float eye[3], look_at[3], up[3];
+    float tan_half;
+    uint32_t key0, key1, stream_tag;
+    int spp;
+    float t_min, t_max;
+    float bg[3];
+    int stack_depth;
+    uint32_t step_limit;
+    float *rgb;
+    int32_t *hit_id;
+    float *hit_t;
+    unsigned long long *counters;
+    uint32_t *status;
+};
+
+// ---------------------------------------------------------------- Philox
+// Philox-4x32-10 (Salmon et al., SC'11): ten rounds, multipliers
+// 0xD2511F53 and 0xCD9E8D57, key increments 0x9E3779B9 and 0xBB67AE85.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ float lane_to_unit(uint32_t u) {
+    return (float)(u >> 8) * 0x1p-24f;
+}
+
+__device__ __forceinline__ uint32_t pick(const uint4 &v, int lane) {
+    return lane == 0 ? v.x : lane == 1 ? v.y : lane == 2 ? v.z : v.w;
+}
+
+// ---------------------------------------------------------------- camera
+// Float32 camera ray with every operation rounded once (no contraction).
+__device__ __forceinline__ void normalise_rn(float v[3]) {
+    float n2 = __fmul_rn(v[0], v[0]);
+    n2 = __fadd_rn(n2, __fmul_rn(v[1], v[1]));
+    n2 = __fadd_rn(n2, __fmul_rn(v[2], v[2]));
+    const float n = __fsqrt_rn(n2);
+    v[0] = __fdiv_rn(v[0], n);
+    v[1] = __fdiv_rn(v[1], n);
+    v[2] = __fdiv_rn(v[2], n);
+}
+
+__device__ __forceinline__ void cross_rn(const float a[3], const float b[3], float c[3]) {
+    c[0] = __fsub_rn(__fmul_rn(a[1], b[2]), __fmul_rn(a[2], b[1]));
+    c[1] = __fsub_rn(__fmul_rn(a[2], b[0]), __fmul_rn(a[0], b[2]));
+    c[2] = __fsub_rn(__fmul_rn(a[0], b[1]), __fmul_rn(a[1], b[0]));
+}
+
+__device__ __forceinline__ void camera_ray(const TraceArgs &a, int x, int y, float d[3]) {
+    float f[3], r[3], u[3];
+    for (int i = 0; i < 3; ++i) f[i] = __fsub_rn(a.look_at[i], a.eye[i]);
+    normalise_rn(f);
+    cross_rn(f, a.up, r);
+    normalise_rn(r);
+    cross_rn(r, f, u);
+    const float s = __fdiv_rn(a.tan_half, (float)a.height);
+    const float ux = __fmul_rn((float)(2 * x + 1 - a.width), s);
+    const float uy = __fmul_rn((float)(a.height - 1 - 2 * y), s);
+    for (int i = 0; i < 3; ++i)
+        d[i] = __fadd_rn(__fadd_rn(f[i], __fmul_rn(ux, r[i])), __fmul_rn(uy, u[i]));
+    normalise_rn(d);
+}
+
+// ---------------------------------------------------------------- SH colour
+__device__ __forceinline__ float load_coef(const void *sh, int dtype, int64_t i) {
+    if (dtype == GS_SH_F32) return __ldg(static_cast<const float *>(sh) + i);
+    const unsigned short raw = __ldg(static_cast<const unsigned short *>(sh) + i);
+    if (dtype == GS_SH_F16) return __half2float(__ushort_as_half(raw));
+    return __uint_as_float((uint32_t)raw << 16);  // bfloat16
+}
+
+// Real spherical harmonics with the Condon-Shortley phase as polynomials in
+// the unit direction (x, y, z); constants are the normalisations
+// sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!), times sqrt(2) for m != 0, times the
+// Legendre polynomial coefficients. The DC term is pre-multiplied (basis 1).
+__device__ void sh_basis(int deg, const float d[3], float Y[16]) {
+    const float x = d[0], y = d[1], z = d[2];
+    Y[0] = 1.0f;
+    if (deg < 1) return;
+    const float c1 = 0.48860251190291992f;  // sqrt(3/(4 pi))
+    Y[1] = -c1 * y;
+    Y[2] = c1 * z;
+    Y[3] = -c1 * x;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = 1.0925484305920792f * x * y;              // sqrt(15/(4 pi))
+    Y[5] = -1.0925484305920792f * y * z;
+    Y[6] = 0.31539156525252005f * (3.0f * zz - 1.0f);  // sqrt(5/(16 pi))
+    Y[7] = -1.0925484305920792f * x * z;
+    Y[8] = 0.54627421529603959f * (xx - yy);          // sqrt(15/(16 pi))
+    if (deg < 3) return;
+    Y[9] = -0.59004358992664352f * y * (3.0f * xx - yy);  // sqrt(35/(32 pi))
+    Y[10] = 2.8906114426405538f * x * y * z;               // sqrt(105/(4 pi))
+    Y[11] = -0.45704579946446572f * y * (5.0f * zz - 1.0f);  // sqrt(21/(32 pi))
+    Y[12] = 0.37317633259011540f * z * (5.0f * zz - 3.0f);   // sqrt(7/(16 pi))
+    Y[13] = -0.45704579946446572f * x * (5.0f * zz - 1.0f);
+    Y[14] = 1.4453057213202769f * z * (xx - yy);            // sqrt(105/(16 pi))
+    Y[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
+}
+
+__device__ __forceinline__ void sh_colour(const TraceArgs &a, uint32_t gid, const float Y[16],
+                                          float c[3]) {
+    const int K = (a.sh_degree + 1) * (a.sh_degree + 1);
+    const int64_t base = (int64_t)gid * K * 3;
+    float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f;
+    if (a.sh_dtype == GS_SH_F32 && K == 16) {
+        const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(a.sh) + base);
+        float v[48];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            const float4 q = __ldg(p + i);
+            v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            acc0 = fmaf(Y[k], v[3 * k], acc0);
+            acc1 = fmaf(Y[k], v[3 * k + 1], acc1);
+            acc2 = fmaf(Y[k], v[3 * k + 2], acc2);
+        }
+    } else {
+        for (int k = 0; k < K; ++k) {
+            acc0 = fmaf(Y[k], load_coef(a.sh, a.sh_dtype, base + 3 * k), acc0);
+            acc1 = fmaf(Y[k], load_coef(a.sh, a.sh_dtype, base + 3 * k + 1), acc1);
+            acc2 = fmaf(Y[k], load_coef(a.sh, a.sh_dtype, base + 3 * k + 2), acc2);
+        }
+    }
+    c[0] = fmaxf(acc0, 0.0f);
+    c[1] = fmaxf(acc1, 0.0f);
+    c[2] = fmaxf(acc2, 0.0f);
+}
+
+// ---------------------------------------------------------------- slots
+struct Slot {
+    float t;    // tc + tau, rounded (used for range clipping and output)
+    float tc;   // base-point parameter
+    float tau;  // 1D mean relative to the base point
+    uint32_t gid;
+};
+
+// (tc_a + tau_a, gid_a) < (tc_b + tau_b, gid_b), with the depth difference
+// formed as (tc_a - tc_b) + (tau_a - tau_b).
+__device__ __forceinline__ bool lex_closer(float tc, float tau, uint32_t gid, const Slot &s) {
+    const float dt = (tc - s.tc) + (tau - s.tau);
+    return dt < 0.0f || (dt == 0.0f && gid < s.gid);
+}
+
+template <int N>
+struct Ray {
+    float o[3], d[3], inv[3], oinv[3];
+    uint32_t ray_id;
+    Slot slot[N];
+    float t_far;  // conservative traversal clip
+};
+
+template <int N>
+__device__ __forceinline__ void update_clip(Ray<N> &r, float t_max) {
+    float far = r.slot[0].t;
+#pragma unroll
+    for (int k = 1; k < N; ++k) far = fmaxf(far, r.slot[k].t);
+    far = fminf(far, t_max);
+    // expanded by 2^-19 relative so float32 slab rounding cannot cull a
+    // node holding a hit that is (in exact arithmetic) not behind the clip
+    r.t_far = far + fabsf(far) * 0x1p-19f;
+}
+
+// Alg. 1 for primitive record idx against all N slots of the current pass.
+template <int N, bool COUNT>
+__device__ __forceinline__ void intersect(const TraceArgs &a, Ray<N> &r, uint32_t idx, int pass,
+                                          unsigned long long &n_draws) {
+    const float4 *pp = reinterpret_cast<const float4 *>(a.prims + idx);
+    const float4 p0 = __ldg(pp), p1 = __ldg(pp + 1), p2 = __ldg(pp + 2), p3 = __ldg(pp + 3);
+    const float mu[3] = {p0.x, p0.y, p0.z};
+    const float m[9] = {p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w, p3.x};
+    const uint32_t gid = __float_as_uint(p3.y);
+    // o - mu = h + l exactly (two-sum)
+    float h[3], l[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float s = r.o[i] - mu[i];
+        const float bp = s - r.o[i];
+        const float ap = s - bp;
+        l[i] = (r.o[i] - ap) + (-mu[i] - bp);
+        h[i] = s;
+    }
+    const float tc = -fmaf(h[0], r.d[0], fmaf(h[1], r.d[1], h[2] * r.d[2]));
+    float w[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) w[i] = fmaf(tc, r.d[i], h[i]) + l[i];
+    float md[3], mw[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        md[i] = fmaf(m[3 * i], r.d[0], fmaf(m[3 * i + 1], r.d[1], m[3 * i + 2] * r.d[2]));
+        mw[i] = fmaf(m[3 * i], w[0], fmaf(m[3 * i + 1], w[1], m[3 * i + 2] * w[2]));
+    }
+    const float dd = fmaf(md[0], md[0], fmaf(md[1], md[1], md[2] * md[2]));
+    const float wd = fmaf(mw[0], md[0], fmaf(mw[1], md[1], mw[2] * md[2]));
+    const float inv_dd = 1.0f / dd;
+    const float tau = -wd * inv_dd;
+    const float t = tc + tau;
+    // Alg. 1 range test; t_far only prunes hits behind every slot
+    if (!(t > a.t_min) || !(t < a.t_max) || !(t <= r.t_far)) return;
+    bool closer[N];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        closer[k] = lex_closer(tc, tau, gid, r.slot[k]);
+        any |= closer[k];
+    }
+    if (!any) return;
+    // refine the base point to the 1D mean, then the ellipsoid test (Eq. 2)
+    float w2[3], mw2[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) w2[i] = fmaf(tau, r.d[i], w[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        mw2[i] = fmaf(m[3 * i], w2[0], fmaf(m[3 * i + 1], w2[1], m[3 * i + 2] * w2[2]));
+    const float ww = fmaf(mw2[0], mw2[0], fmaf(mw2[1], mw2[1], mw2[2] * mw2[2]));
+    const float wd2 = fmaf(mw2[0], md[0], fmaf(mw2[1], md[1], mw2[2] * md[2]));
+    const float q = fmaxf(ww - wd2 * wd2 * inv_dd, 0.0f);
+    if (!(q <= kS2)) return;
+    const float alpha = p0.w * expf(-0.5f * q);
+    // Eq. 4: one Philox call serves four consecutive samples
+    uint4 u0 = make_uint4(0, 0, 0, 0), u1 = make_uint4(0, 0, 0, 0);
+    const uint32_t s0 = (uint32_t)pass * N;
+    u0 = philox10(make_uint4(r.ray_id, gid, s0 >> 2, a.stream_tag), a.key0, a.key1);
+    if (N == 8) u1 = philox10(make_uint4(r.ray_id, gid, (s0 >> 2) + 1, a.stream_tag), a.key0, a.key1);
+    if (COUNT) n_draws += 1 + (N == 8);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        if (!closer[k]) continue;
+        const uint32_t s = s0 + k;
+        const uint32_t bits = (N == 8 && k >= 4) ? pick(u1, s & 3) : pick(u0, s & 3);
+        if (lane_to_unit(bits) < alpha) {
+            r.slot[k].t = t;
+            r.slot[k].tc = tc;
+            r.slot[k].tau = tau;
+            r.slot[k].gid = gid;
+        }
+    }
+    update_clip(r, a.t_max);
+}
+
+// Slab test of one child box against [t_min, t_far].
+__device__ __forceinline__ bool slab(const float *lo_hi, const float inv[3], const float oinv[3],
+                                     float t_min, float t_far, float &t_enter) {
+    const float tx0 = fmaf(lo_hi[0], inv[0], -oinv[0]), tx1 = fmaf(lo_hi[3], inv[0], -oinv[0]);
+    const float ty0 = fmaf(lo_hi[1], inv[1], -oinv[1]), ty1 = fmaf(lo_hi[4], inv[1], -oinv[1]);
+    const float tz0 = fmaf(lo_hi[2], inv[2], -oinv[2]), tz1 = fmaf(lo_hi[5], inv[2], -oinv[2]);
+    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), t_min));
+    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), t_far));
+    t_enter = tn;
+    return tn <= tf;
+}
+
+template <int N, bool COUNT>
+__global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // warp-coherent 8x4 pixel sub-tiles, 2x2 of them per 16x8 block tile
+    const int x = blockIdx.x * kTileW + (warp & 1) * 8 + (lane & 7);
+    const int y = blockIdx.y * kTileH + (warp >> 1) * 4 + (lane >> 3);
+    if (x >= a.width || y >= a.height) return;
+    const int64_t pix = (int64_t)y * a.width + x;
+    const int64_t npix = (int64_t)a.width * a.height;
+
+    Ray<N> r;
+    camera_ray(a, x, y, r.d);
+    for (int i = 0; i < 3; ++i) {
+        r.o[i] = a.eye[i];
+        const float di = fabsf(r.d[i]) < 1e-30f ? copysignf(1e-30f, r.d[i]) : r.d[i];
+        r.inv[i] = 1.0f / di;
+        r.oinv[i] = r.o[i] * r.inv[i];
+    }
+    r.ray_id = a.ray_id_offset + (uint32_t)pix;
+    float Y[16];
+    sh_basis(a.sh_degree, r.d, Y);
+
+    unsigned long long n_nodes = 0, n_prims = 0, n_draws = 0;
+    uint32_t err = 0;
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+    uint32_t stack[kMaxStack];
+    float stack_t[kMaxStack];
+
+    for (int pass = 0; pass < a.spp; ++pass) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) r.slot[k] = Slot{INFINITY, INFINITY, 0.0f, 0xffffffffu};
+        update_clip(r, a.t_max);
+        if (a.n_nodes > 0) {
+            int sp = 0;
+            uint32_t node = 0;
+            uint32_t steps = 0;
+            for (;;) {
+                if (++steps > a.step_limit) {
+                    err |= kErrSteps;
+                    break;
+                }
+                if (COUNT) ++n_nodes;
+                const float4 *np = reinterpret_cast<const float4 *>(a.nodes + node);
+                const float4 b0 = __ldg(np), b1 = __ldg(np + 1), b2 = __ldg(np + 2);
+                const uint4 cref = __ldg(reinterpret_cast<const uint4 *>(np + 3));
+                const float boxL[6] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
+                const float boxR[6] = {b1.z, b1.w, b2.x, b2.y, b2.z, b2.w};
+                float tL, tR;
+                bool hL = slab(boxL, r.inv, r.oinv, a.t_min, r.t_far, tL);
+                bool hR = slab(boxR, r.inv, r.oinv, a.t_min, r.t_far, tR);
+                // leaf children: run Alg. 1 now, nearer box first
+                uint32_t leaf0 = 0xffffffffu, leaf1 = 0xffffffffu;
+                if (hL && (cref.x & kLeafBit)) { leaf0 = cref.x & ~kLeafBit; hL = false; }
+                if (hR && (cref.y & kLeafBit)) {
+                    if (leaf0 == 0xffffffffu) leaf0 = cref.y & ~kLeafBit;
+                    else if (tR < tL) { leaf1 = leaf0; leaf0 = cref.y & ~kLeafBit; }
+                    else leaf1 = cref.y & ~kLeafBit;
+                    hR = false;
+                }
+                if (leaf0 != 0xffffffffu) {
+                    for (int li = 0; li < 2; ++li) {
+                        const uint32_t leaf = li == 0 ? leaf0 : leaf1;
+                        if (leaf == 0xffffffffu) break;
+                        if (COUNT) ++n_prims;
+                        intersect<N, COUNT>(a, r, leaf, pass, n_draws);
+                    }
+                    hL = hL && tL <= r.t_far;
+                    hR = hR && tR <= r.t_far;
+                }
+                if (hL && hR) {
+                    uint32_t nearc = cref.x, farc = cref.y;
+                    float far_t = tR;
+                    if (tR < tL) { nearc = cref.y; farc = cref.x; far_t = tL; }
+                    if (sp >= a.stack_depth) {
+                        err |= kErrStack;
+                        break;
+                    }
+                    stack[sp] = farc;
+                    stack_t[sp] = far_t;
+                    ++sp;
+                    node = nearc;
+                    continue;
+                }
+                if (hL) { node = cref.x; continue; }
+                if (hR) { node = cref.y; continue; }
+                bool found = false;
+                while (sp > 0) {
+                    --sp;
+                    if (stack_t[sp] <= r.t_far) {
+                        node = stack[sp];
+                        found = true;
+                        break;
+                    }
+                }
+                if (!found) break;
+            }
+        }
+        // shade each slot once (Eq. 6) and accumulate (Eq. 7)
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            float c[3];
+            if (r.slot[k].gid != 0xffffffffu) {
+                sh_colour(a, r.slot[k].gid, Y, c);
+            } else {
+                c[0] = a.bg[0]; c[1] = a.bg[1]; c[2] = a.bg[2];
+            }
+            acc[0] += c[0];
+            acc[1] += c[1];
+            acc[2] += c[2];
+            if (a.hit_id) {
+                const int64_t o = ((int64_t)pass * N + k) * npix + pix;
+                a.hit_id[o] = r.slot[k].gid == 0xffffffffu ? -1 : (int32_t)r.slot[k].gid;
+                a.hit_t[o] = r.slot[k].t;
+            }
+        }
+    }
+    const float inv_n = 1.0f / (float)((int64_t)a.spp * N);
+    a.rgb[3 * pix + 0] = acc[0] * inv_n;
+    a.rgb[3 * pix + 1] = acc[1] * inv_n;
+    a.rgb[3 * pix + 2] = acc[2] * inv_n;
+    if (err) atomicOr(a.status, err);
+    if (COUNT) {
+        atomicAdd(a.counters + 0, n_nodes);
+        atomicAdd(a.counters + 1, n_prims);
+        atomicAdd(a.counters + 2, n_draws);
+        atomicAdd(a.counters + 3, 1ull);
+    }
+}
+
+template <int N>
+void launch_n(const TraceArgs &a, bool count, cudaStream_t s) {
+    dim3 grid((a.width + kTileW - 1) / kTileW, (a.height + kTileH - 1) / kTileH);
+    if (count) k_trace<N, true><<<grid, kThreads, 0, s>>>(a);
+    else k_trace<N, false><<<grid, kThreads, 0, s>>>(a);
+}
+
+}  // namespace
+
+gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
+                       const gs_trace_params *p, float *rgb, int32_t *hit_id, float *hit_t,
+                       cudaStream_t s) {
+    TraceArgs a;
+    a.nodes = b->nodes;
+    a.prims = b->prims;
+    a.sh = g->sh;
+    a.n_nodes = b->n_nodes;
+    a.sh_degree = g->sh_degree;
+    a.sh_dtype = g->sh_dtype;
+    a.width = cam->width;
+    a.height = cam->height;
+    a.ray_id_offset = cam->ray_id_offset;
+    for (int i = 0; i < 3; ++i) {
+        a.eye[i] = cam->eye[i];
+        a.look_at[i] = cam->look_at[i];
+        a.up[i] = cam->up[i];
+        a.bg[i] = p->bg[i];
+    }
+    a.tan_half = (float)tan((double)cam->fov_y_deg * 3.14159265358979323846 / 360.0);
+    a.key0 = (uint32_t)(p->seed & 0xffffffffu);
+    a.key1 = (uint32_t)(p->seed >> 32);
+    a.stream_tag = p->stream_tag;
+    a.spp = p->spp;
+    a.t_min = p->t_min;
+    a.t_max = p->t_max;
+    a.stack_depth = p->stack_depth == 0 ? kMaxStack : p->stack_depth;
+    // a valid traversal visits every internal node at most once per pass
+    a.step_limit = (uint32_t)(b->n_nodes + 8 < (int64_t)kStepLimit ? b->n_nodes + 8 : kStepLimit);
+    a.rgb = rgb;
+    a.hit_id = hit_id;
+    a.hit_t = hit_t;
+    a.counters = p->counters;
+    a.status = b->status;
+    const bool count = p->counters != nullptr;
+    switch (p->n_hits) {
+        case 1: launch_n<1>(a, count, s); break;
+        case 2: launch_n<2>(a, count, s); break;
+        case 4: launch_n<4>(a, count, s); break;
+        case 8: launch_n<8>(a, count, s); break;
+        default: return fail(GS_ERR_INVALID_ARG, "n_hits must be 1, 2, 4 or 8");
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "trace launch");
+    return GS_OK;
+}
+
+}  // namespace gsrt

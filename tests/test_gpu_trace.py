@@ -1,0 +1,92 @@
+"""GPU parity of gs_trace_stochastic against the FP64 oracle: per-sample
+hit ids (>= 99.99% agreement, every mismatch of class i), colours within
+1e-5 relative, plus invariances of the keyed draws."""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+from tests import _parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gs():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_06598_gb300 as m
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for gpu tests")
+    return m
+
+
+def _run(gs, cloud, cam, spp, n_hits, seed=0, **kw):
+    g = gs.Gaussians.from_cloud(cloud)
+    bvh = gs.build_bvh(g)
+    rgb, hid, ht = gs.trace_stochastic(bvh, g, cam, seed=seed, spp=spp, n_hits=n_hits,
+                                       want_hits=True, **kw)
+    bvh.sync_status()
+    npix = cam.width * cam.height
+    S = spp * n_hits
+    ids = hid.cpu().numpy().reshape(S, npix).T
+    ts = ht.cpu().numpy().reshape(S, npix).T
+    out = rgb.cpu().numpy().reshape(npix, 3)
+    bvh.free()
+    return out, ids, ts
+
+
+def _assert_parity(gs, cloud, cam, spp, n_hits, seed=0, pixels=None):
+    rgb, ids, ts = _run(gs, cloud, cam, spp, n_hits, seed)
+    if pixels is None:
+        pixels = np.arange(cam.width * cam.height)
+    ref = oracle.render_pinhole(cloud, cam, scenes.TraceSettings(seed=seed, spp=spp, n_hits=n_hits),
+                                pixels=pixels)
+    agree, classes, details = _parity.compare(cloud, cam, seed, ids[pixels], ref, pixels)
+    assert agree >= 0.9999, (agree, classes, details[:10])
+    assert set(classes) <= {"i"}, (classes, [d for d in details if d[4] != "i"][:10])
+    same = np.all(ids[pixels] == ref["hit_id"], axis=1)
+    assert colour_ok(rgb[pixels], ref["est"], same)
+    # depths of agreeing hits
+    hit = (ids[pixels] == ref["hit_id"]) & (ref["hit_id"] >= 0)
+    assert np.allclose(ts[pixels][hit], ref["hit_t"][hit], rtol=2e-6, atol=1e-6)
+    return agree, classes
+
+
+def colour_ok(g, r, same):
+    v = _parity.colour_check(g, r, same)
+    assert v <= 0.0, v
+    return True
+
+
+@pytest.mark.parametrize("spp,n_hits", [(1, 1), (16, 1), (4, 4), (2, 8), (3, 2)])
+def test_tiny_parity(gs, spp, n_hits):
+    cloud = scenes.tiny_cloud(0)
+    cam = scenes.default_camera(64, 64)
+    _assert_parity(gs, cloud, cam, spp, n_hits)
+
+
+def test_shell_small_ragged(gs):
+    """Clustered shell cloud, image size not a multiple of the 16x8 tile."""
+    cloud = scenes.shell_cloud(1, M=20000)
+    cam = scenes.default_camera(100, 61)
+    _assert_parity(gs, cloud, cam, spp=4, n_hits=1, seed=5)
+
+
+def test_passes_by_hits_invariance(gs):
+    cloud = scenes.shell_cloud(2, M=5000)
+    cam = scenes.default_camera(48, 40)
+    _, a, ta = _run(gs, cloud, cam, spp=8, n_hits=1, seed=9)
+    _, b, tb = _run(gs, cloud, cam, spp=2, n_hits=4, seed=9)
+    _, c, tc = _run(gs, cloud, cam, spp=1, n_hits=8, seed=9)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    assert np.array_equal(ta, tb) and np.array_equal(ta, tc)
+
+
+def test_deterministic(gs):
+    cloud = scenes.shell_cloud(3, M=5000)
+    cam = scenes.default_camera(40, 30)
+    r1, a1, _ = _run(gs, cloud, cam, spp=3, n_hits=4, seed=1)
+    r2, a2, _ = _run(gs, cloud, cam, spp=3, n_hits=4, seed=1)
+    assert np.array_equal(a1, a2) and np.array_equal(r1, r2)
