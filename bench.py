@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Throughput of stochastic ray tracing of transparent 3D Gaussians.
+
+Workload: 1,000,000 Gaussians in 64 clusters on a unit-sphere shell (SH
+degree 3, float32), one 1920x1080 pinhole view from distance 3, 60 degree
+vertical FOV. One step = hierarchy rebuild over all Gaussians + one
+stochastic trace of the view with N=1 and spp=64 (the benchmark spec's metric);
+N=4 at spp=16 (the same 64 samples per pixel) is timed the same way and
+reported beside it.
+
+Metric: Mrays/s = width * height * spp / step time, one ray = one traversal.
+RMSE against the exact sorted blend (computed by the FP64 oracle on a fixed
+16,384-pixel subset) is reported for N=1 and for N=4 at equal trace time.
+
+``--impl reference`` times the FP64 CPU oracle instead, on a bounded pixel
+sample of the same workload per step.
+
+Multi-GPU (torchrun): every rank renders its own view (distinct ray ids), no
+collective on the data path; scaling is weak.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W_IMG, H_IMG, M_GAUSS = 1920, 1080, 1_000_000
+SPP_N1, SPP_N4 = 64, 16
+RMSE_PIXELS = 16384
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-pixels", type=int, default=512,
+                    help="pixels per step of the reference (oracle) arm")
+    ap.add_argument("--case", choices=["trace-1080p"], default=None,
+                    help="run one small profiling case instead of the benchmark")
+    ap.add_argument("--n-hits", type=int, default=1, help="N of the profiling case")
+    return ap.parse_args()
+
+
+def run_case(args):
+    """Profiling case: the 1M-Gaussian shell, the 1920x1080 view, spp=1,
+    traced twice (warm-up launch, then the launch to capture)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_06598_gb300 as gs
+    import scenes
+    cloud = scenes.shell_cloud(0, M=M_GAUSS)
+    g = gs.Gaussians.from_cloud(cloud)
+    bvh = gs.build_bvh(g)
+    cam = gs.Camera(W_IMG, H_IMG)
+    for _ in range(2):
+        gs.trace_stochastic(bvh, g, cam, seed=0, spp=1, n_hits=args.n_hits)
+    bvh.sync_status()
+    torch.cuda.synchronize()
+    bvh.free()
+    print("case trace-1080p done")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def config_dict(args, world):
+    return {"workload": "shell-1M-1080p", "gaussians": M_GAUSS, "sh_degree": 3,
+            "clusters": 64, "width": W_IMG, "height": H_IMG, "spp": SPP_N1, "n_hits": 1,
+            "views_per_gpu": 1, "parallelism": "dp%d (rays sharded by view)" % world,
+            "l2": "flushed between timed steps (512 MiB write)"}
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def trace_source_hash():
+    h = hashlib.sha256()
+    for name in ("trace.cu", "gsrt_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2504_06598_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(n_hits):
+    """DRAM bytes per launch of the trace kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "trace_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != trace_source_hash():
+        return None
+    entry = rec.get("n%d" % n_hits)
+    return None if entry is None else entry.get("dram_bytes_per_launch")
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle, timed on the host cores on bounded pixel samples."""
+    if rank != 0:
+        return
+    import oracle
+    import scenes
+    oracle.build()
+    cloud = scenes.shell_cloud(0, M=M_GAUSS)
+    cam = scenes.default_camera(W_IMG, H_IMG)
+    st = scenes.TraceSettings(seed=0, spp=SPP_N1, n_hits=1)
+    rng = np.random.default_rng(7)
+    times = []
+    threads = 0
+    for step in range(args.warmup + args.steps):
+        pix = np.sort(rng.choice(W_IMG * H_IMG, size=args.ref_pixels, replace=False))
+        t0 = time.perf_counter()
+        r = oracle.render_pinhole(cloud, cam, st, pixels=pix, want_hits=False)
+        dt = time.perf_counter() - t0
+        threads = r["threads"]
+        if step >= args.warmup:
+            times.append(dt)
+    rays = args.ref_pixels * SPP_N1
+    value = rays / float(np.mean(times)) / 1e6
+    line = {"impl": "reference", "metric": "Mrays/s at 1M Gaussians 1080p (N=1,4); RMSE vs exact blend at equal time",
+            "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, world),
+            "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+                             "sample": "%d random pixels of the 1080p view per step, spp=64, "
+                                       "brute force over all 1M Gaussians" % args.ref_pixels},
+            "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.case:
+        run_case(args)
+        return
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_06598_gb300 as gs
+    import scenes
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    cloud = scenes.shell_cloud(0, M=M_GAUSS)
+    npix = W_IMG * H_IMG
+    cam = gs.Camera(W_IMG, H_IMG, ray_id_offset=rank * npix)
+    g = gs.Gaussians.from_cloud(cloud)
+    bvh = gs.build_bvh(g)
+    bvh.sync_status()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    rgb = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32, device=dev)
+
+    def step(n_hits, spp, events=None):
+        if events:
+            events[0].record(stream)
+        bvh.rebuild(g)
+        if events:
+            events[1].record(stream)
+        gs.trace_stochastic(bvh, g, cam, seed=0, spp=spp, n_hits=n_hits, out=rgb)
+        if events:
+            events[2].record(stream)
+
+    # instrumented launches (untimed): node / primitive / shading counts
+    visits = {}
+    for n_hits, spp in ((1, SPP_N1), (4, SPP_N4)):
+        cnt = torch.zeros(5, dtype=torch.int64, device=dev)
+        gs.trace_stochastic(bvh, g, cam, seed=0, spp=spp, n_hits=n_hits, out=rgb, counters=cnt)
+        bvh.sync_status()
+        c = cnt.cpu().numpy().astype(np.float64)
+        visits[n_hits] = {"nodes": c[0], "prims": c[1], "philox": c[2], "rays": c[3],
+                          "shaded": c[4], "spp": spp}
+
+    def timed(n_hits, spp):
+        for _ in range(args.warmup):
+            step(n_hits, spp)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        with ClockSampler(local) as clk:
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                step(n_hits, spp, evs[k])
+            torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        build = np.array([a.elapsed_time(b) for a, b, _ in evs])
+        trace = np.array([b.elapsed_time(c) for _, b, c in evs])
+        res = {"step_ms": float(np.mean(build + trace)), "build_ms": float(np.mean(build)),
+               "trace_ms": float(np.mean(trace)), "clocks": clk.summary()}
+        if dist:
+            t = torch.tensor([res["step_ms"], res["trace_ms"]], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            res["step_ms"], res["trace_ms"] = float(t[0]), float(t[1])
+        return res
+
+    bvh.sync_status()
+    r1 = timed(1, SPP_N1)
+    r4 = timed(4, SPP_N4)
+    bvh.sync_status()
+
+    # end to end through the public API: pinned host inputs, result read back
+    host = {k: getattr(g, k).cpu().pin_memory() for k in
+            ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    rgb_host = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = rgb_host.numel() * 4
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for name, t in host.items():
+            getattr(g, name).copy_(t, non_blocking=True)
+        bvh.rebuild(g)
+        gs.trace_stochastic(bvh, g, cam, seed=0, spp=SPP_N1, n_hits=1, out=rgb)
+        rgb_host.copy_(rgb, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    bvh.sync_status()
+    e2e_mean = float(np.mean(e2e_ms))
+    if dist:
+        t = torch.tensor([e2e_mean], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_mean = float(t[0])
+
+    rays_step = npix * SPP_N1 * world
+    value = rays_step / (r1["step_ms"] * 1e-3) / 1e6
+    launches_per_step = 29
+
+    # roofline of the trace kernel: algorithmic bytes per launch / duration
+    peak, peak_kind = measured_peak()
+    info = bvh.info()
+    sh_bytes = 16 * 3 * 4
+
+    def roof(v, trace_ms, n_hits):
+        alg = (info["node_bytes"] * v["nodes"] + info["prim_bytes"] * v["prims"]
+               + sh_bytes * v["shaded"] + 12 * npix)
+        ach = alg / (trace_ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": recorded_traffic(n_hits),
+                "alg_bytes_per_launch": alg, "peak_kind": peak_kind,
+                "kernel": "k_trace<%d>" % n_hits}
+
+    line = {
+        "metric": "Mrays/s at 1M Gaussians 1080p (N=1,4); RMSE vs exact blend at equal time",
+        "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r1["step_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(args, world), "clocks": r1["clocks"],
+        "e2e": {"value": rays_step / (e2e_mean * 1e-3) / 1e6, "unit": "Mrays/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": e2e_mean},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": roof(visits[1], r1["trace_ms"], 1),
+        "build_ms": r1["build_ms"], "trace_ms": r1["trace_ms"],
+        "trace_mrays_per_s": npix * SPP_N1 / (r1["trace_ms"] * 1e-3) / 1e6,
+        "visits_per_ray": {"nodes": visits[1]["nodes"] / visits[1]["rays"] / SPP_N1,
+                           "prims": visits[1]["prims"] / visits[1]["rays"] / SPP_N1,
+                           "philox": visits[1]["philox"] / visits[1]["rays"] / SPP_N1},
+        "n4": {"spp": SPP_N4, "samples_per_pixel": SPP_N4 * 4, "ms_per_step": r4["step_ms"],
+               "trace_ms": r4["trace_ms"],
+               "mrays_per_s": npix * SPP_N4 * world / (r4["step_ms"] * 1e-3) / 1e6,
+               "msamples_per_s": npix * SPP_N4 * 4 * world / (r4["step_ms"] * 1e-3) / 1e6,
+               "roofline": roof(visits[4], r4["trace_ms"], 4),
+               "visits_per_ray": {"nodes": visits[4]["nodes"] / visits[4]["rays"] / SPP_N4,
+                                  "prims": visits[4]["prims"] / visits[4]["rays"] / SPP_N4},
+               "clocks": r4["clocks"]},
+        "msamples_per_s_n1": value,
+    }
+
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        pix = scenes.pixel_subset(W_IMG, H_IMG, RMSE_PIXELS)
+        ocam = scenes.default_camera(W_IMG, H_IMG, ray_id_offset=rank * npix)
+        t0 = time.perf_counter()
+        ref = oracle.render_pinhole(cloud, ocam, scenes.TraceSettings(seed=0, spp=SPP_N1),
+                                    pixels=pix, want_hits=False)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": RMSE_PIXELS * SPP_N1 / dt / 1e6, "unit": "Mrays/s",
+                                "cores": ref["threads"], "kind": "oracle",
+                                "sample": "fixed seeded subset of %d pixels of the 1080p view, "
+                                          "spp=64, brute force over all 1M Gaussians (%.1f s)"
+                                          % (RMSE_PIXELS, dt)}
+        blend = ref["blend"]
+        # RMSE vs the exact blend: N=1 at spp=64, N=4 at equal trace time
+        gs.trace_stochastic(bvh, g, cam, seed=0, spp=SPP_N1, n_hits=1, out=rgb)
+        img1 = rgb.reshape(-1, 3)[torch.from_numpy(pix).to(dev)].cpu().numpy()
+        t1_per_spp = r1["trace_ms"] / SPP_N1
+        t4_per_spp = r4["trace_ms"] / SPP_N4
+        spp_eq = max(1, int(round(SPP_N1 * t1_per_spp / t4_per_spp)))
+        gs.trace_stochastic(bvh, g, cam, seed=0, spp=spp_eq, n_hits=4, out=rgb)
+        img4 = rgb.reshape(-1, 3)[torch.from_numpy(pix).to(dev)].cpu().numpy()
+        bvh.sync_status()
+        rmse = lambda a: float(np.sqrt(np.mean((a - blend) ** 2)))  # noqa: E731
+        line["rmse_vs_blend"] = {
+            "pixels": RMSE_PIXELS,
+            "n1": {"spp": SPP_N1, "rmse": rmse(img1), "trace_ms": r1["trace_ms"]},
+            "n4": {"spp": spp_eq, "samples": spp_eq * 4, "rmse": rmse(img4),
+                   "trace_ms_est": t4_per_spp * spp_eq},
+            "oracle_estimator_n1": {"rmse": rmse(ref["est"])},
+        }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    bvh.free()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

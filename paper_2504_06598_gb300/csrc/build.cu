@@ -2,7 +2,9 @@
 // (Sec. 3.2 builds a BVH over the boxes of Eq. 2; the paper delegates it to
 // Embree/OptiX, here it is a linear BVH built on the GPU):
 //   k_preprocess  box of each Gaussian's bounding ellipsoid + scene bounds
-//   k_morton      63-bit Morton code of each mean in the scene bounds
+//   k_morton      63-bit key: Morton code of each mean in the scene bounds
+//                 with a size class of the Gaussian's box below the top
+//                 two octree levels
 //   radix sort    stable LSD sort of (code, id), 8 passes of 8 bits
 //   k_karras      binary radix tree over the sorted codes (Karras 2012),
 //                 equal codes split by position
@@ -145,21 +147,43 @@ __device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
     return v;
 }
 
+// Sort key of one Gaussian: its 63-bit Morton code with a 4-bit size class
+// inserted below the top two octree levels (6 bits). Gaussians of very
+// different extent then fall into different subtrees below the coarse
+// spatial split, so a few large Gaussians no longer inflate the boxes of
+// the many small ones around them. Size class = floor(-2 log2(e / E)),
+// clamped to 0..15, with e the largest box edge of the Gaussian and E the
+// largest edge of the bounds of the means (large Gaussians sort first).
+constexpr int kKeyTopBits = 6;
+constexpr int kKeySizeBits = 4;
+
 __global__ void k_morton(int64_t M, const float *__restrict__ means,
-                         const unsigned int *__restrict__ bounds,
+                         const unsigned int *__restrict__ bounds, const float *__restrict__ aabb,
                          unsigned long long *__restrict__ codes, uint32_t *__restrict__ vals) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= M) return;
     unsigned long long q[3];
+    float scene = 0.0f, edge = 0.0f;
     for (int k = 0; k < 3; ++k) {
         float lo = ord2f(bounds[k]), hi = ord2f(bounds[3 + k]);
         float ext = hi - lo;
+        scene = fmaxf(scene, ext);
+        edge = fmaxf(edge, aabb[6 * g + 3 + k] - aabb[6 * g + k]);
         float x = means[3 * g + k];
         float u = (ext > 0.0f) ? (x - lo) / ext : 0.0f;
         u = fminf(fmaxf(u, 0.0f), 1.0f);  // NaN -> 0
         q[k] = (unsigned long long)(u * 2097151.0f);
     }
-    codes[g] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+    const unsigned long long morton = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+    int cls = 0;
+    if (scene > 0.0f && edge > 0.0f) {
+        const float c = floorf(-2.0f * log2f(edge / scene));
+        cls = (int)fminf(fmaxf(c, 0.0f), (float)((1 << kKeySizeBits) - 1));
+    }
+    const int low = 63 - kKeyTopBits - kKeySizeBits;
+    const unsigned long long top = morton >> (63 - kKeyTopBits);
+    const unsigned long long rest = (morton & ((1ull << (63 - kKeyTopBits)) - 1ull)) >> kKeySizeBits;
+    codes[g] = (top << (63 - kKeyTopBits)) | ((unsigned long long)cls << low) | rest;
     vals[g] = (uint32_t)g;
 }
 
@@ -394,7 +418,8 @@ gs_status build_into(gs_bvh *b, const gs_gaussians *g, cudaStream_t s) {
         return cuda_fail(e, "memset bounds");
     k_preprocess<<<grid_for(M, 256), 256, 0, s>>>(M, g->means, g->log_scales, g->quats,
                                                    g->opacity_logits, b->aabb, b->bounds, b->status);
-    k_morton<<<grid_for(M, 256), 256, 0, s>>>(M, g->means, b->bounds, b->codes[0], b->vals[0]);
+    k_morton<<<grid_for(M, 256), 256, 0, s>>>(M, g->means, b->bounds, b->aabb, b->codes[0],
+                                               b->vals[0]);
     const int64_t tiles = radix_tiles(M);
     int cur = 0;
     for (int shift = 0; shift < 64; shift += 8) {

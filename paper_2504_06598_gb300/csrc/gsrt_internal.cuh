@@ -5,7 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/gsrt.h"
+#include "gsrt.h"
 
 namespace gsrt {
 

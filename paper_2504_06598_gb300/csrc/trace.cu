@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
     float Y[16];
     sh_basis(a.sh_degree, r.d, Y);
 
-    unsigned long long n_nodes = 0, n_prims = 0, n_draws = 0;
+    unsigned long long n_nodes = 0, n_prims = 0, n_draws = 0, n_shaded = 0;
     uint32_t err = 0;
     float acc[3] = {0.0f, 0.0f, 0.0f};
     uint32_t stack[kMaxStack];
@@ -410,6 +410,7 @@ __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
             float c[3];
             if (r.slot[k].gid != 0xffffffffu) {
                 sh_colour(a, r.slot[k].gid, Y, c);
+                if (COUNT) ++n_shaded;
             } else {
                 c[0] = a.bg[0]; c[1] = a.bg[1]; c[2] = a.bg[2];
             }
@@ -433,6 +434,7 @@ __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
         atomicAdd(a.counters + 1, n_prims);
         atomicAdd(a.counters + 2, n_draws);
         atomicAdd(a.counters + 3, 1ull);
+        atomicAdd(a.counters + 4, n_shaded);
     }
 }
 
