@@ -109,9 +109,10 @@ typedef struct gs_pinhole {
  *   depth_mode    0: depth is the mean of the 1D Gaussian (Sec. 3.1)
  *   stack_depth   traversal stack entries per ray, 1..64 (0 = 64)
  *   stream_tag    fourth Philox counter word, separates ray streams
- *   counters      optional device uint64[4], incremented by the launch:
- *                 {nodes visited, primitives tested, Philox draws, rays};
- *                 NULL disables counting (the default fast path). */
+ *   counters      optional device uint64[5], incremented by the launch:
+ *                 {nodes visited, primitives tested, Philox calls, rays,
+ *                 samples shaded with a Gaussian's colour}; NULL disables
+ *                 counting (the default fast path). */
 typedef struct gs_trace_params {
     uint64_t seed;
     int32_t spp;

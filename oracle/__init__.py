@@ -80,7 +80,7 @@ def _load():
             lib.orc_camera_ray.argtypes = [P, C.c_int32, C.c_int32, P, P, P]
             lib.orc_closest_accepted.restype = C.c_int64
             lib.orc_closest_accepted.argtypes = [C.c_int64, P, P, P, P]
-            lib.orc_blend.argtypes = [C.c_int64, P, P, P, P, P, P]
+            lib.orc_blend.argtypes = [C.c_int64, P, P, P, P, P, P, P]
             lib.orc_enumerate_expectation.restype = C.c_int
             lib.orc_enumerate_expectation.argtypes = [C.c_int, P, P, P, P]
             lib.orc_ray_candidates.restype = C.c_int64
@@ -88,9 +88,9 @@ def _load():
                                                P, P, P, P, P]
             lib.orc_max_threads.restype = C.c_int
             lib.orc_render_pinhole.restype = C.c_int
-            lib.orc_render_pinhole.argtypes = [P, P, P, C.c_int64, P, P, P, P, P, P, C.c_int]
+            lib.orc_render_pinhole.argtypes = [P, P, P, C.c_int64, P, P, P, P, P, P, P, C.c_int]
             lib.orc_render_rays.restype = C.c_int
-            lib.orc_render_rays.argtypes = [P, P, C.c_int64, P, P, P, P, P, P, P, P, C.c_int]
+            lib.orc_render_rays.argtypes = [P, P, C.c_int64, P, P, P, P, P, P, P, P, P, C.c_int]
             _lib = lib
     return _lib
 
@@ -209,7 +209,8 @@ def closest_accepted(t, gid, accepted, order=None) -> int:
     return int(lib.orc_closest_accepted(len(t), _ptr(t), _ptr(g), _ptr(a), _ptr(o)))
 
 
-def blend(t, gid, alpha, rgb, bg=(0.0, 0.0, 0.0)):
+def blend(t, gid, alpha, rgb, bg=(0.0, 0.0, 0.0), second_moment=False):
+    """Eq. 3 (with background); optionally also E[L^2] of one sample."""
     lib = _load()
     t = _c(t, np.float64)
     g = _c(gid, np.int32)
@@ -217,8 +218,9 @@ def blend(t, gid, alpha, rgb, bg=(0.0, 0.0, 0.0)):
     c = _c(rgb, np.float64).reshape(-1, 3)
     b = _c(bg, np.float64)
     out = np.zeros(3)
-    lib.orc_blend(len(t), _ptr(t), _ptr(g), _ptr(a), _ptr(c), _ptr(b), _ptr(out))
-    return out
+    out2 = np.zeros(3)
+    lib.orc_blend(len(t), _ptr(t), _ptr(g), _ptr(a), _ptr(c), _ptr(b), _ptr(out), _ptr(out2))
+    return (out, out2) if second_moment else out
 
 
 def enumerate_expectation(alpha, rgb, bg=(0.0, 0.0, 0.0)):
@@ -259,7 +261,9 @@ def max_threads() -> int:
 def render_pinhole(cloud, cam, settings, pixels=None, want_hits=True, n_threads=0):
     """Brute-force render of the listed linear pixel indices (all by default).
 
-    Returns a dict with ``blend`` [n,3], ``est`` [n,3], ``hit_id`` [n,S],
+    Returns a dict with ``blend`` [n,3], ``blend2`` [n,3] (second moment of
+    one sample, so the per-sample variance is blend2 - blend^2), ``est`` [n,3],
+    ``hit_id`` [n,S],
     ``hit_t`` [n,S] (S = spp * n_hits, sample s = pass * n_hits + k),
     ``n_valid`` [n] and ``threads``."""
     lib = _load()
@@ -270,6 +274,7 @@ def render_pinhole(cloud, cam, settings, pixels=None, want_hits=True, n_threads=
     n = len(pix)
     S = int(settings.spp) * int(settings.n_hits)
     blend_o = np.zeros((n, 3))
+    blend2 = np.zeros((n, 3))
     est = np.zeros((n, 3))
     hid = np.zeros((n, S), np.int32) if want_hits else None
     ht = np.zeros((n, S)) if want_hits else None
@@ -277,9 +282,10 @@ def render_pinhole(cloud, cam, settings, pixels=None, want_hits=True, n_threads=
     cs = _pinhole(cam)
     ps = _params(settings)
     used = lib.orc_render_pinhole(h.ref, C.byref(cs), C.byref(ps), n, _ptr(pix), _ptr(blend_o),
-                                  _ptr(est), _ptr(hid), _ptr(ht), _ptr(nv), int(n_threads))
-    return {"blend": blend_o, "est": est, "hit_id": hid, "hit_t": ht, "n_valid": nv,
-            "threads": int(used)}
+                                  _ptr(blend2), _ptr(est), _ptr(hid), _ptr(ht), _ptr(nv),
+                                  int(n_threads))
+    return {"blend": blend_o, "blend2": blend2, "est": est, "hit_id": hid, "hit_t": ht,
+            "n_valid": nv, "threads": int(used)}
 
 
 def render_rays(cloud, origins, dirs, ray_ids, settings, want_hits=True, n_threads=0):
@@ -292,13 +298,14 @@ def render_rays(cloud, origins, dirs, ray_ids, settings, want_hits=True, n_threa
     n = len(rid)
     S = int(settings.spp) * int(settings.n_hits)
     blend_o = np.zeros((n, 3))
+    blend2 = np.zeros((n, 3))
     est = np.zeros((n, 3))
     hid = np.zeros((n, S), np.int32) if want_hits else None
     ht = np.zeros((n, S)) if want_hits else None
     nv = np.zeros(n, np.int64)
     ps = _params(settings)
     used = lib.orc_render_rays(h.ref, C.byref(ps), n, _ptr(o), _ptr(d), _ptr(rid),
-                               _ptr(blend_o), _ptr(est), _ptr(hid), _ptr(ht), _ptr(nv),
-                               int(n_threads))
-    return {"blend": blend_o, "est": est, "hit_id": hid, "hit_t": ht, "n_valid": nv,
-            "threads": int(used)}
+                               _ptr(blend_o), _ptr(blend2), _ptr(est), _ptr(hid), _ptr(ht),
+                               _ptr(nv), int(n_threads))
+    return {"blend": blend_o, "blend2": blend2, "est": est, "hit_id": hid, "hit_t": ht,
+            "n_valid": nv, "threads": int(used)}

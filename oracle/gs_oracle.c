@@ -385,21 +385,32 @@ int64_t orc_closest_accepted(int64_t n, const double *t, const int32_t *gid,
     return win;
 }
 
-/* Eq. 3 with background: candidates are sorted by (t, gid) first. */
-static void blend_sorted(int64_t n, const orc_cand *c, const double bg[3], double out[3])
+/* Eq. 3 with background: candidates are sorted by (t, gid) first. The
+ * optional second output is the same composite of squared colours, which is
+ * E[L^2] of the single-sample estimate of Eq. 6: sample s returns c_i with
+ * probability T_i alpha_i and bg with probability T_{M+1}. */
+static void blend_sorted(int64_t n, const orc_cand *c, const double bg[3], double out[3],
+                         double *out2)
 {
     double T = 1.0;
     double L[3] = {0.0, 0.0, 0.0};
+    double L2[3] = {0.0, 0.0, 0.0};
     for (int64_t i = 0; i < n; ++i) {
-        for (int ch = 0; ch < 3; ++ch) L[ch] += T * c[i].alpha * c[i].rgb[ch];
+        for (int ch = 0; ch < 3; ++ch) {
+            L[ch] += T * c[i].alpha * c[i].rgb[ch];
+            L2[ch] += T * c[i].alpha * c[i].rgb[ch] * c[i].rgb[ch];
+        }
         T *= (1.0 - c[i].alpha);
     }
-    for (int ch = 0; ch < 3; ++ch) out[ch] = L[ch] + T * bg[ch];
+    for (int ch = 0; ch < 3; ++ch) {
+        out[ch] = L[ch] + T * bg[ch];
+        if (out2) out2[ch] = L2[ch] + T * bg[ch] * bg[ch];
+    }
 }
 
 /* Exported: Eq. 3 on arbitrary (unsorted) candidate arrays. */
 void orc_blend(int64_t n, const double *t, const int32_t *gid, const double *alpha,
-               const double *rgb, const double bg[3], double out[3])
+               const double *rgb, const double bg[3], double out[3], double *out2)
 {
     orc_cand *c = (orc_cand *)malloc((size_t)(n > 0 ? n : 1) * sizeof(orc_cand));
     for (int64_t i = 0; i < n; ++i) {
@@ -409,7 +420,7 @@ void orc_blend(int64_t n, const double *t, const int32_t *gid, const double *alp
         for (int ch = 0; ch < 3; ++ch) c[i].rgb[ch] = rgb[3 * i + ch];
     }
     qsort(c, (size_t)n, sizeof(orc_cand), cand_cmp);
-    blend_sorted(n, c, bg, out);
+    blend_sorted(n, c, bg, out, out2);
     free(c);
 }
 
@@ -504,7 +515,8 @@ int64_t orc_ray_candidates(const orc_scene *sc, const double o[3], const double 
  * averaged (Eq. 7). Sample s uses draw xi(seed, ray_id, gid, s). */
 static void trace_one(const orc_scene *sc, const orc_gauss *act, const orc_params *p,
                       const double o[3], const double d[3], uint32_t ray_id, cand_list *L,
-                      double blend[3], double est[3], int32_t *hit_id, double *hit_t)
+                      double blend[3], double *blend2, double est[3], int32_t *hit_id,
+                      double *hit_t)
 {
     collect(sc, act, o, d, p->t_min, p->t_max, L);
     int64_t S = (int64_t)p->spp * p->n_hits;
@@ -524,7 +536,7 @@ static void trace_one(const orc_scene *sc, const orc_gauss *act, const orc_param
         for (int ch = 0; ch < 3; ++ch) est[ch] = S > 0 ? acc[ch] / (double)S : 0.0;
     if (blend) {
         qsort(L->v, (size_t)L->n, sizeof(orc_cand), cand_cmp);
-        blend_sorted(L->n, L->v, p->bg, blend);
+        blend_sorted(L->n, L->v, p->bg, blend, blend2);
     }
 }
 
@@ -542,8 +554,9 @@ int orc_max_threads(void)
  *   blend [n][3], est [n][3], hit_id [n][S], hit_t [n][S], n_valid [n].
  * Returns the number of threads used. */
 int orc_render_pinhole(const orc_scene *sc, const orc_pinhole *cam, const orc_params *p,
-                       int64_t n_pix, const int64_t *pix, double *blend, double *est,
-                       int32_t *hit_id, double *hit_t, int64_t *n_valid, int n_threads)
+                       int64_t n_pix, const int64_t *pix, double *blend, double *blend2,
+                       double *est, int32_t *hit_id, double *hit_t, int64_t *n_valid,
+                       int n_threads)
 {
     orc_gauss *act = activate_all(sc);
     int64_t S = (int64_t)p->spp * p->n_hits;
@@ -566,7 +579,8 @@ int orc_render_pinhole(const orc_scene *sc, const orc_pinhole *cam, const orc_pa
             double o[3], d[3];
             uint32_t rid;
             orc_camera_ray(cam, x, y, o, d, &rid);
-            trace_one(sc, act, p, o, d, rid, &L, blend ? blend + 3 * i : 0, est ? est + 3 * i : 0,
+            trace_one(sc, act, p, o, d, rid, &L, blend ? blend + 3 * i : 0,
+                      blend2 ? blend2 + 3 * i : 0, est ? est + 3 * i : 0,
                       hit_id ? hit_id + S * i : 0, hit_t ? hit_t + S * i : 0);
             if (n_valid) n_valid[i] = L.n;
         }
@@ -579,8 +593,9 @@ int orc_render_pinhole(const orc_scene *sc, const orc_pinhole *cam, const orc_pa
 /* Exported: same for explicit rays (origins/dirs given as float32 values,
  * dirs of unit length), ray_ids[i] keys the draws of ray i. */
 int orc_render_rays(const orc_scene *sc, const orc_params *p, int64_t n_rays, const float *origins,
-                    const float *dirs, const uint32_t *ray_ids, double *blend, double *est,
-                    int32_t *hit_id, double *hit_t, int64_t *n_valid, int n_threads)
+                    const float *dirs, const uint32_t *ray_ids, double *blend, double *blend2,
+                    double *est, int32_t *hit_id, double *hit_t, int64_t *n_valid,
+                    int n_threads)
 {
     orc_gauss *act = activate_all(sc);
     int64_t S = (int64_t)p->spp * p->n_hits;
@@ -605,8 +620,8 @@ int orc_render_rays(const orc_scene *sc, const orc_params *p, int64_t n_rays, co
                 d[k] = (double)dirs[3 * i + k];
             }
             trace_one(sc, act, p, o, d, ray_ids[i], &L, blend ? blend + 3 * i : 0,
-                      est ? est + 3 * i : 0, hit_id ? hit_id + S * i : 0,
-                      hit_t ? hit_t + S * i : 0);
+                      blend2 ? blend2 + 3 * i : 0, est ? est + 3 * i : 0,
+                      hit_id ? hit_id + S * i : 0, hit_t ? hit_t + S * i : 0);
             if (n_valid) n_valid[i] = L.n;
         }
         free(L.v);

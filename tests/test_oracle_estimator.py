@@ -84,6 +84,20 @@ def test_enumeration_equals_blend(oracle_lib):
         assert np.allclose(got, want, atol=1e-12)
 
 
+def test_second_moment_by_enumeration(oracle_lib):
+    """E[L^2] of one sample: the 2^n enumeration with squared colours equals
+    the composite of squared colours returned beside the blend."""
+    rng = np.random.default_rng(5)
+    for n in [1, 4, 9]:
+        alpha = rng.uniform(0, 1, n)
+        rgb = rng.uniform(0, 1, (n, 3))
+        bg = rng.uniform(0, 1, 3)
+        t = rng.uniform(1, 5, n)
+        want = oracle_lib.enumerate_expectation(alpha[np.argsort(t)], rgb[np.argsort(t)] ** 2, bg ** 2)
+        _, got = oracle_lib.blend(t, np.arange(n, dtype=np.int32), alpha, rgb, bg, second_moment=True)
+        assert np.allclose(got, want, atol=1e-12)
+
+
 def _tiny_setup(spp):
     cl = scenes.tiny_cloud(0)
     cam = scenes.default_camera(16, 16)
@@ -140,7 +154,8 @@ def test_blend_matches_candidates(oracle_lib):
 @pytest.mark.slow
 def test_estimator_converges_to_blend(oracle_lib):
     """Unbiasedness (Eq. 5): the 4096-sample mean is within a few standard
-    errors of the exact blend; z-scores pool to mean ~0, variance ~1."""
+    errors of the exact blend; z-scores pool to mean ~0, variance ~1. The
+    sample variance also matches the exact one (blend2 - blend^2)."""
     cl = scenes.tiny_cloud(0)
     cam = scenes.default_camera(32, 32)
     st = scenes.TraceSettings(seed=1, spp=4096)
@@ -156,6 +171,8 @@ def test_estimator_converges_to_blend(oracle_lib):
         lut = {int(g): c["rgb"][k] for k, g in enumerate(c["gid"])}
         cols = np.array([lut[int(g)] if g >= 0 else np.zeros(3) for g in r["hit_id"][i]])
         se = cols.std(axis=0, ddof=1) / np.sqrt(len(cols))
+        var_exact = r["blend2"][i] - r["blend"][i] ** 2
+        assert np.all(np.abs(cols.var(axis=0, ddof=1) - var_exact) <= 0.15 * var_exact + 2e-3)
         for ch in range(3):
             if se[ch] == 0:
                 assert r["est"][i, ch] == pytest.approx(r["blend"][i, ch], abs=1e-12)
