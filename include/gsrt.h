@@ -198,6 +198,33 @@ gs_status gs_trace_stochastic(const gs_bvh *bvh, const gs_gaussians *g, const gs
                               const gs_trace_params *p, float *rgb_out, int32_t *hit_id_out,
                               float *hit_t_out, void *stream);
 
+/* Allocation-free variant of gs_build_bvh. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- for
+ * example a renderer thread that must never trigger the implicit device
+ * synchronisation an allocation can cause, or a host application that hands
+ * every byte of device memory to its own pool allocator up front.
+ *
+ * It runs the same kernels as gs_build_bvh and writes the same hierarchy,
+ * byte for byte, into buffers the caller owns:
+ *   g          Gaussian parameters (device arrays), 0 <= M <= 65536;
+ *              larger M returns GS_ERR_INVALID_ARG (use gs_build_bvh)
+ *   nodes_out  device, max(M-1, 1) * 64 bytes, 16-byte aligned: node
+ *              records in the gs_bvh_export layout, node 0 the root
+ *   prims_out  device, M * 64 bytes, 16-byte aligned: Gaussian records
+ *   status_out optional device uint32: the caller clears it; the build ORs
+ *              error bits into it (non-zero means a non-finite parameter)
+ *   stream     where the kernels are enqueued
+ * Scratch memory lives in one statically allocated device array of this
+ * library (about 4 MB on every GPU that loads the library, held until the
+ * process exits). The first call on each device looks up that array's
+ * device address (cudaGetSymbolAddress), so make it before any stream
+ * capture. Every call shares the array: calls whose work overlaps on the
+ * GPU (different streams, or different host threads) race and corrupt each
+ * other; serialise them, for example on one stream. No cudaMalloc, cudaFree
+ * or other allocating call is made. */
+gs_status gs_build_bvh_noalloc(const gs_gaussians *g, void *nodes_out, void *prims_out,
+                               uint32_t *status_out, void *stream);
+
 /* Short description of a status code (static string). */
 const char *gs_status_string(gs_status s);
 

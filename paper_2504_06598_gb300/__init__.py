@@ -76,6 +76,8 @@ _SIGNATURES = {
     "gs_bvh_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gs_trace_stochastic": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_build_bvh_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p]),
     "gs_status_string": (C.c_char_p, [C.c_int]),
     "gs_last_error": (C.c_char_p, []),
 }
