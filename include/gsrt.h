@@ -193,7 +193,9 @@ gs_status gs_bvh_export(const gs_bvh *bvh, void *nodes_out, void *prims_out,
  *   hit_t_out  device float[spp][n_hits][height][width] depth of each
  *              sample's hit (ray parameter, d is unit length) or +inf;
  *              NULL to skip
- * Deterministic: identical inputs give bit-identical outputs. */
+ * Deterministic: identical inputs give bit-identical outputs. Traces that use
+ * the same handle share its tile counter and status word, so they must not
+ * overlap on the GPU: issue them on one stream (or order their streams). */
 gs_status gs_trace_stochastic(const gs_bvh *bvh, const gs_gaussians *g, const gs_pinhole *cam,
                               const gs_trace_params *p, float *rgb_out, int32_t *hit_id_out,
                               float *hit_t_out, void *stream);

@@ -27,7 +27,10 @@ def nvcc_path() -> str:
 
 
 def _flags(extra=()):
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-I", INCLUDE,
+    # -fmad=false: no implicit multiply-add contraction, so every template
+    # instantiation of a kernel rounds identically; fused operations are
+    # written explicitly (fmaf) where the arithmetic wants them.
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-I", INCLUDE,
                    "-Xcompiler", "-fPIC,-ffp-contract=off", *extra]
 
 

@@ -1,6 +1,7 @@
 // trace.cu -- stochastic ray tracing of transparent Gaussians on sm_103a.
 //
-// One thread per pixel. Each pass is one traversal of the hierarchy
+// One thread per pixel, one warp per 8x4 pixel tile, traversing as a packet
+// (see traverse_packet). Each pass is one traversal of the hierarchy
 // (Sec. 3.2) keeping N closest accepted intersections (Sec. 3.5). At every
 // leaf the intersection routine of Alg. 1 runs:
 //   t    mean of the 1D Gaussian along the ray (Sec. 3.1)
@@ -32,7 +33,7 @@
 namespace gsrt {
 namespace {
 
-constexpr int kTileW = 16, kTileH = 8, kThreads = 128;
+constexpr int kThreads = 128;
 
 struct TraceArgs {
     const Node *nodes;
@@ -56,6 +57,7 @@ struct TraceArgs {
     float *hit_t;
     unsigned long long *counters;
     uint32_t *status;
+    uint32_t *work;  // tile counter of the persistent launch
 };
 
 // ---------------------------------------------------------------- Philox
@@ -307,142 +309,187 @@ __device__ __forceinline__ bool slab(const float *lo_hi, const float inv[3], con
     return tn <= tf;
 }
 
+// Packet traversal of one 8x4 pixel tile by one warp (same pass for all
+// lanes). The warp visits the union of the nodes its lanes need: every node
+// is fetched once for the whole warp (one broadcast load), each lane
+// slab-tests the children against its own clipped range and keeps its own
+// slots, and the warp descends while any lane still needs a child. A lane's
+// stack entry remembers its own entry distance, so a popped node is skipped
+// once every lane's clip has passed it. Each lane runs Alg. 1 on exactly
+// the leaves its own ray reaches, so per-lane results are those of an
+// independent traversal.
+template <int N, bool COUNT>
+__device__ __forceinline__ void traverse_packet(const TraceArgs &a, Ray<N> &r, int pass,
+                                                uint32_t *stack, float *stack_t, uint32_t &err,
+                                                unsigned long long &n_nodes,
+                                                unsigned long long &n_prims,
+                                                unsigned long long &n_draws) {
+    const uint32_t kAll = 0xffffffffu;
+    int sp = 0;
+    uint32_t node = 0, steps = 0;
+    for (;;) {
+        if (++steps > a.step_limit) {
+            err |= kErrSteps;
+            break;
+        }
+        if (COUNT) ++n_nodes;
+        const float4 *np = reinterpret_cast<const float4 *>(a.nodes + node);
+        const float4 b0 = __ldg(np), b1 = __ldg(np + 1), b2 = __ldg(np + 2);
+        const uint4 cref = __ldg(reinterpret_cast<const uint4 *>(np + 3));
+        const float boxL[6] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
+        const float boxR[6] = {b1.z, b1.w, b2.x, b2.y, b2.z, b2.w};
+        float tL, tR;
+        bool hL = slab(boxL, r.inv, r.oinv, a.t_min, r.t_far, tL);
+        bool hR = slab(boxR, r.inv, r.oinv, a.t_min, r.t_far, tR);
+        const bool leafL = (cref.x & kLeafBit) != 0u, leafR = (cref.y & kLeafBit) != 0u;
+        if (leafL || leafR) {
+            // Alg. 1 on the leaves this lane's ray reaches, nearer box first
+            const bool swap = leafL && leafR && hR && (!hL || tR < tL);
+            for (int li = 0; li < 2; ++li) {
+                const bool right = (li == 0) == swap;
+                if (!(right ? leafR : leafL) || !(right ? hR : hL)) continue;
+                if (COUNT) ++n_prims;
+                intersect<N, COUNT>(a, r, (right ? cref.y : cref.x) & ~kLeafBit, pass, n_draws);
+            }
+            if (leafL) hL = false;
+            if (leafR) hR = false;
+            hL = hL && tL <= r.t_far;
+            hR = hR && tR <= r.t_far;
+        }
+        const unsigned mL = __ballot_sync(kAll, hL), mR = __ballot_sync(kAll, hR);
+        if (mL && mR) {
+            // the child most lanes enter first is visited first
+            const unsigned lf = __ballot_sync(kAll, hL && (!hR || tL <= tR));
+            const bool left_first = 2 * __popc(lf) >= __popc(mL | mR);
+            if (sp >= a.stack_depth) {
+                err |= kErrStack;
+                break;
+            }
+            stack[sp] = left_first ? cref.y : cref.x;
+            stack_t[sp] = left_first ? (hR ? tR : INFINITY) : (hL ? tL : INFINITY);
+            ++sp;
+            node = left_first ? cref.x : cref.y;
+            continue;
+        }
+        if (mL) { node = cref.x; continue; }
+        if (mR) { node = cref.y; continue; }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (__any_sync(kAll, stack_t[sp] <= r.t_far)) {
+                node = stack[sp];
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+    }
+}
+
+// Persistent kernel: each warp repeatedly takes the next 8x4 pixel tile
+// (one atomic per tile, so the tail of the launch stays balanced), then
+// runs all passes of its 32 pixels.
 template <int N, bool COUNT>
 __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // warp-coherent 8x4 pixel sub-tiles, 2x2 of them per 16x8 block tile
-    const int x = blockIdx.x * kTileW + (warp & 1) * 8 + (lane & 7);
-    const int y = blockIdx.y * kTileH + (warp >> 1) * 4 + (lane >> 3);
-    if (x >= a.width || y >= a.height) return;
-    const int64_t pix = (int64_t)y * a.width + x;
+    const int lane = threadIdx.x & 31;
+    const uint32_t kAll = 0xffffffffu;
+    const uint32_t tiles_x = (a.width + 7) / 8, tiles_y = (a.height + 3) / 4;
+    const uint32_t n_tiles = tiles_x * tiles_y;
     const int64_t npix = (int64_t)a.width * a.height;
-
-    Ray<N> r;
-    camera_ray(a, x, y, r.d);
-    for (int i = 0; i < 3; ++i) {
-        r.o[i] = a.eye[i];
-        const float di = fabsf(r.d[i]) < 1e-30f ? copysignf(1e-30f, r.d[i]) : r.d[i];
-        r.inv[i] = 1.0f / di;
-        r.oinv[i] = r.o[i] * r.inv[i];
-    }
-    r.ray_id = a.ray_id_offset + (uint32_t)pix;
-    float Y[16];
-    sh_basis(a.sh_degree, r.d, Y);
-
-    unsigned long long n_nodes = 0, n_prims = 0, n_draws = 0, n_shaded = 0;
-    uint32_t err = 0;
-    float acc[3] = {0.0f, 0.0f, 0.0f};
     uint32_t stack[kMaxStack];
     float stack_t[kMaxStack];
-
-    for (int pass = 0; pass < a.spp; ++pass) {
-#pragma unroll
-        for (int k = 0; k < N; ++k) r.slot[k] = Slot{INFINITY, INFINITY, 0.0f, 0xffffffffu};
-        update_clip(r, a.t_max);
-        if (a.n_nodes > 0) {
-            int sp = 0;
-            uint32_t node = 0;
-            uint32_t steps = 0;
-            for (;;) {
-                if (++steps > a.step_limit) {
-                    err |= kErrSteps;
-                    break;
-                }
-                if (COUNT) ++n_nodes;
-                const float4 *np = reinterpret_cast<const float4 *>(a.nodes + node);
-                const float4 b0 = __ldg(np), b1 = __ldg(np + 1), b2 = __ldg(np + 2);
-                const uint4 cref = __ldg(reinterpret_cast<const uint4 *>(np + 3));
-                const float boxL[6] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
-                const float boxR[6] = {b1.z, b1.w, b2.x, b2.y, b2.z, b2.w};
-                float tL, tR;
-                bool hL = slab(boxL, r.inv, r.oinv, a.t_min, r.t_far, tL);
-                bool hR = slab(boxR, r.inv, r.oinv, a.t_min, r.t_far, tR);
-                // leaf children: run Alg. 1 now, nearer box first
-                uint32_t leaf0 = 0xffffffffu, leaf1 = 0xffffffffu;
-                if (hL && (cref.x & kLeafBit)) { leaf0 = cref.x & ~kLeafBit; hL = false; }
-                if (hR && (cref.y & kLeafBit)) {
-                    if (leaf0 == 0xffffffffu) leaf0 = cref.y & ~kLeafBit;
-                    else if (tR < tL) { leaf1 = leaf0; leaf0 = cref.y & ~kLeafBit; }
-                    else leaf1 = cref.y & ~kLeafBit;
-                    hR = false;
-                }
-                if (leaf0 != 0xffffffffu) {
-                    for (int li = 0; li < 2; ++li) {
-                        const uint32_t leaf = li == 0 ? leaf0 : leaf1;
-                        if (leaf == 0xffffffffu) break;
-                        if (COUNT) ++n_prims;
-                        intersect<N, COUNT>(a, r, leaf, pass, n_draws);
-                    }
-                    hL = hL && tL <= r.t_far;
-                    hR = hR && tR <= r.t_far;
-                }
-                if (hL && hR) {
-                    uint32_t nearc = cref.x, farc = cref.y;
-                    float far_t = tR;
-                    if (tR < tL) { nearc = cref.y; farc = cref.x; far_t = tL; }
-                    if (sp >= a.stack_depth) {
-                        err |= kErrStack;
-                        break;
-                    }
-                    stack[sp] = farc;
-                    stack_t[sp] = far_t;
-                    ++sp;
-                    node = nearc;
-                    continue;
-                }
-                if (hL) { node = cref.x; continue; }
-                if (hR) { node = cref.y; continue; }
-                bool found = false;
-                while (sp > 0) {
-                    --sp;
-                    if (stack_t[sp] <= r.t_far) {
-                        node = stack[sp];
-                        found = true;
-                        break;
-                    }
-                }
-                if (!found) break;
-            }
+    uint32_t err = 0;
+    unsigned long long n_nodes = 0, n_prims = 0, n_draws = 0, n_shaded = 0, n_rays = 0;
+    for (;;) {
+        uint32_t tile = 0;
+        if (lane == 0) tile = atomicAdd(a.work, 1u);
+        tile = __shfl_sync(kAll, tile, 0);
+        if (tile >= n_tiles) break;
+        const int x = (int)((tile % tiles_x) * 8 + (lane & 7));
+        const int y = (int)((tile / tiles_x) * 4 + (lane >> 3));
+        const bool valid = x < a.width && y < a.height;
+        const int64_t pix = valid ? (int64_t)y * a.width + x : 0;
+        Ray<N> r;
+        camera_ray(a, valid ? x : 0, valid ? y : 0, r.d);
+        for (int i = 0; i < 3; ++i) {
+            r.o[i] = a.eye[i];
+            const float di = fabsf(r.d[i]) < 1e-30f ? copysignf(1e-30f, r.d[i]) : r.d[i];
+            r.inv[i] = 1.0f / di;
+            r.oinv[i] = r.o[i] * r.inv[i];
         }
-        // shade each slot once (Eq. 6) and accumulate (Eq. 7)
+        r.ray_id = a.ray_id_offset + (uint32_t)pix;
+        float acc[3] = {0.0f, 0.0f, 0.0f};
+        for (int pass = 0; pass < a.spp; ++pass) {
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-            float c[3];
-            if (r.slot[k].gid != 0xffffffffu) {
-                sh_colour(a, r.slot[k].gid, Y, c);
-                if (COUNT) ++n_shaded;
-            } else {
-                c[0] = a.bg[0]; c[1] = a.bg[1]; c[2] = a.bg[2];
+            for (int k = 0; k < N; ++k) r.slot[k] = Slot{INFINITY, INFINITY, 0.0f, 0xffffffffu};
+            update_clip(r, a.t_max);
+            if (!valid) r.t_far = -INFINITY;  // lanes off the image never hit
+            if (a.n_nodes > 0)
+                traverse_packet<N, COUNT>(a, r, pass, stack, stack_t, err, n_nodes, n_prims,
+                                          n_draws);
+            if (valid) {
+                // shade each slot once (Eq. 6) and accumulate (Eq. 7)
+                float Y[16];
+                sh_basis(a.sh_degree, r.d, Y);
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    float c[3];
+                    if (r.slot[k].gid != 0xffffffffu) {
+                        sh_colour(a, r.slot[k].gid, Y, c);
+                        if (COUNT) ++n_shaded;
+                    } else {
+                        c[0] = a.bg[0]; c[1] = a.bg[1]; c[2] = a.bg[2];
+                    }
+                    acc[0] += c[0];
+                    acc[1] += c[1];
+                    acc[2] += c[2];
+                    if (a.hit_id) {
+                        const int64_t o = ((int64_t)pass * N + k) * npix + pix;
+                        a.hit_id[o] = r.slot[k].gid == 0xffffffffu ? -1 : (int32_t)r.slot[k].gid;
+                        a.hit_t[o] = r.slot[k].t;
+                    }
+                }
             }
-            acc[0] += c[0];
-            acc[1] += c[1];
-            acc[2] += c[2];
-            if (a.hit_id) {
-                const int64_t o = ((int64_t)pass * N + k) * npix + pix;
-                a.hit_id[o] = r.slot[k].gid == 0xffffffffu ? -1 : (int32_t)r.slot[k].gid;
-                a.hit_t[o] = r.slot[k].t;
-            }
+            __syncwarp();
+        }
+        if (valid) {
+            const float inv_n = 1.0f / (float)((int64_t)a.spp * N);
+            a.rgb[3 * pix + 0] = acc[0] * inv_n;
+            a.rgb[3 * pix + 1] = acc[1] * inv_n;
+            a.rgb[3 * pix + 2] = acc[2] * inv_n;
+            if (COUNT) ++n_rays;
         }
     }
-    const float inv_n = 1.0f / (float)((int64_t)a.spp * N);
-    a.rgb[3 * pix + 0] = acc[0] * inv_n;
-    a.rgb[3 * pix + 1] = acc[1] * inv_n;
-    a.rgb[3 * pix + 2] = acc[2] * inv_n;
     if (err) atomicOr(a.status, err);
     if (COUNT) {
         atomicAdd(a.counters + 0, n_nodes);
         atomicAdd(a.counters + 1, n_prims);
         atomicAdd(a.counters + 2, n_draws);
-        atomicAdd(a.counters + 3, 1ull);
+        atomicAdd(a.counters + 3, n_rays);
         atomicAdd(a.counters + 4, n_shaded);
     }
 }
 
 template <int N>
-void launch_n(const TraceArgs &a, bool count, cudaStream_t s) {
-    dim3 grid((a.width + kTileW - 1) / kTileW, (a.height + kTileH - 1) / kTileH);
-    if (count) k_trace<N, true><<<grid, kThreads, 0, s>>>(a);
-    else k_trace<N, false><<<grid, kThreads, 0, s>>>(a);
+gs_status launch_n(const TraceArgs &a, bool count, cudaStream_t s) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = count ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<N, true>, kThreads, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<N, false>, kThreads, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "trace launch setup");
+    // one resident grid; warps take tiles until none is left
+    const uint32_t tiles = (uint32_t)(((a.width + 7) / 8) * ((a.height + 3) / 4));
+    const uint32_t warps_needed = tiles;
+    uint32_t blocks = (uint32_t)sms * (uint32_t)(per > 0 ? per : 1);
+    const uint32_t max_blocks = (warps_needed + kThreads / 32 - 1) / (kThreads / 32);
+    if (blocks > max_blocks) blocks = max_blocks;
+    if ((e = cudaMemsetAsync(a.work, 0, sizeof(uint32_t), s)) != cudaSuccess)
+        return cuda_fail(e, "reset work counter");
+    if (count) k_trace<N, true><<<blocks, kThreads, 0, s>>>(a);
+    else k_trace<N, false><<<blocks, kThreads, 0, s>>>(a);
+    return GS_OK;
 }
 
 }  // namespace
@@ -481,14 +528,17 @@ gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole 
     a.hit_t = hit_t;
     a.counters = p->counters;
     a.status = b->status;
+    a.work = b->status + 1;
     const bool count = p->counters != nullptr;
+    gs_status st;
     switch (p->n_hits) {
-        case 1: launch_n<1>(a, count, s); break;
-        case 2: launch_n<2>(a, count, s); break;
-        case 4: launch_n<4>(a, count, s); break;
-        case 8: launch_n<8>(a, count, s); break;
+        case 1: st = launch_n<1>(a, count, s); break;
+        case 2: st = launch_n<2>(a, count, s); break;
+        case 4: st = launch_n<4>(a, count, s); break;
+        case 8: st = launch_n<8>(a, count, s); break;
         default: return fail(GS_ERR_INVALID_ARG, "n_hits must be 1, 2, 4 or 8");
     }
+    if (st != GS_OK) return st;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "trace launch");
     return GS_OK;
