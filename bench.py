@@ -257,12 +257,12 @@ def main():
     # instrumented launches (untimed): node / primitive / shading counts
     visits = {}
     for n_hits, spp in ((1, SPP_N1), (4, SPP_N4)):
-        cnt = torch.zeros(5, dtype=torch.int64, device=dev)
+        cnt = torch.zeros(7, dtype=torch.int64, device=dev)
         gs.trace_stochastic(bvh, g, cam, seed=0, spp=spp, n_hits=n_hits, out=rgb, counters=cnt)
         bvh.sync_status()
         c = cnt.cpu().numpy().astype(np.float64)
         visits[n_hits] = {"nodes": c[0], "prims": c[1], "philox": c[2], "rays": c[3],
-                          "shaded": c[4], "spp": spp}
+                          "shaded": c[4], "node_fetch": c[5], "prim_fetch": c[6], "spp": spp}
 
     def timed(n_hits, spp):
         for _ in range(args.warmup):
@@ -332,13 +332,19 @@ def main():
     sh_bytes = 16 * 3 * 4
 
     def roof(v, trace_ms, n_hits):
+        # per-ray algorithmic bytes: each ray's own node entries and Gaussian
+        # tests, one SH record per shaded sample, the pixel's output
         alg = (info["node_bytes"] * v["nodes"] + info["prim_bytes"] * v["prims"]
                + sh_bytes * v["shaded"] + 12 * npix)
+        # bytes the warps actually request (a node or record once per warp)
+        warp = (info["node_bytes"] * v["node_fetch"] + info["prim_bytes"] * v["prim_fetch"]
+                + sh_bytes * v["shaded"] + 12 * npix)
         ach = alg / (trace_ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "traffic": recorded_traffic(n_hits),
-                "alg_bytes_per_launch": alg, "peak_kind": peak_kind,
-                "kernel": "k_trace<%d>" % n_hits}
+                "alg_bytes_per_launch": alg, "warp_request_bytes_per_launch": warp,
+                "warp_request_gbs": warp / (trace_ms * 1e-3) / 1e9,
+                "peak_kind": peak_kind, "kernel": "k_trace<%d>" % n_hits}
 
     line = {
         "metric": "Mrays/s at 1M Gaussians 1080p (N=1,4); RMSE vs exact blend at equal time",
@@ -355,7 +361,8 @@ def main():
         "trace_mrays_per_s": npix * SPP_N1 / (r1["trace_ms"] * 1e-3) / 1e6,
         "visits_per_ray": {"nodes": visits[1]["nodes"] / visits[1]["rays"] / SPP_N1,
                            "prims": visits[1]["prims"] / visits[1]["rays"] / SPP_N1,
-                           "philox": visits[1]["philox"] / visits[1]["rays"] / SPP_N1},
+                           "philox": visits[1]["philox"] / visits[1]["rays"] / SPP_N1,
+                           "warp_node_fetches_per_ray": visits[1]["node_fetch"] / visits[1]["rays"] / SPP_N1},
         "n4": {"spp": SPP_N4, "samples_per_pixel": SPP_N4 * 4, "ms_per_step": r4["step_ms"],
                "trace_ms": r4["trace_ms"],
                "mrays_per_s": npix * SPP_N4 * world / (r4["step_ms"] * 1e-3) / 1e6,

@@ -109,10 +109,12 @@ typedef struct gs_pinhole {
  *   depth_mode    0: depth is the mean of the 1D Gaussian (Sec. 3.1)
  *   stack_depth   traversal stack entries per ray, 1..64 (0 = 64)
  *   stream_tag    fourth Philox counter word, separates ray streams
- *   counters      optional device uint64[5], incremented by the launch:
- *                 {nodes visited, primitives tested, Philox calls, rays,
- *                 samples shaded with a Gaussian's colour}; NULL disables
- *                 counting (the default fast path). */
+ *   counters      optional device uint64[7], incremented by the launch:
+ *                 {nodes entered by each ray's own traversal, Gaussians
+ *                 tested (Alg. 1 runs), Philox calls, rays (pixels),
+ *                 samples shaded with a Gaussian's colour, node records
+ *                 fetched by warps, Gaussian records fetched by warps};
+ *                 NULL disables counting (the default fast path). */
 typedef struct gs_trace_params {
     uint64_t seed;
     int32_t spp;

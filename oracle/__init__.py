@@ -89,6 +89,9 @@ def _load():
             lib.orc_max_threads.restype = C.c_int
             lib.orc_render_pinhole.restype = C.c_int
             lib.orc_render_pinhole.argtypes = [P, P, P, C.c_int64, P, P, P, P, P, P, P, C.c_int]
+            lib.orc_grad_pinhole.restype = C.c_int
+            lib.orc_grad_pinhole.argtypes = [P, P, P, C.c_int64, P, P, C.c_int, P, P, P, P, P,
+                                             C.c_int]
             lib.orc_render_rays.restype = C.c_int
             lib.orc_render_rays.argtypes = [P, P, C.c_int64, P, P, P, P, P, P, P, P, P, C.c_int]
             _lib = lib
@@ -309,3 +312,31 @@ def render_rays(cloud, origins, dirs, ray_ids, settings, want_hits=True, n_threa
                                _ptr(nv), int(n_threads))
     return {"blend": blend_o, "blend2": blend2, "est": est, "hit_id": hid, "hit_t": ht,
             "n_valid": nv, "threads": int(used)}
+
+
+# ---------------------------------------------------------------- gradients
+
+def grad_pinhole(cloud, cam, settings, d_rgb, pixels=None, mode="blend", n_threads=0):
+    """Gradient of sum_p d_rgb[p] . L_p w.r.t. every parameter (FP64).
+
+    mode "blend": exact sorted blend (Eq. 3); mode "estimator": the
+    stochastic estimate averaged over the spp * n_hits samples of each pixel
+    with the same draws as rendering. Returns a dict of arrays shaped like
+    the parameters (means, log_scales, quats, opacity_logits, sh)."""
+    lib = _load()
+    h = _SceneHandle(cloud)
+    if pixels is None:
+        pixels = np.arange(cam.width * cam.height, dtype=np.int64)
+    pix = _c(pixels, np.int64)
+    g = _c(d_rgb, np.float64).reshape(-1, 3)
+    assert len(g) == len(pix)
+    M = cloud.M
+    out = {"means": np.zeros((M, 3)), "log_scales": np.zeros((M, 3)), "quats": np.zeros((M, 4)),
+           "opacity_logits": np.zeros(M), "sh": np.zeros(cloud.sh.shape)}
+    cs = _pinhole(cam)
+    ps = _params(settings)
+    lib.orc_grad_pinhole(h.ref, C.byref(cs), C.byref(ps), len(pix), _ptr(pix), _ptr(g),
+                         0 if mode == "blend" else 1, _ptr(out["means"]), _ptr(out["log_scales"]),
+                         _ptr(out["quats"]), _ptr(out["opacity_logits"]), _ptr(out["sh"]),
+                         int(n_threads))
+    return out

@@ -629,3 +629,233 @@ int orc_render_rays(const orc_scene *sc, const orc_params *p, int64_t n_rays, co
     free(act);
     return used;
 }
+
+/* ------------------------------------------------------------------ */
+/* Gradients (the paper's closing remark on differentiable rendering,  */
+/* Sec. 6). For a scalar G = sum_rays g . L with g the given per-ray     */
+/* weight (dLoss/dL), parameters theta_i = (mu[3], log_s[3], quat[4],    */
+/* logit) and SH coefficients k_i of every Gaussian.                     */
+/*                                                                       */
+/* alpha = o exp(-q/2), o = sigmoid(logit), q = v^T Sigma^-1 v with      */
+/* v = o_ray + t* d - mu at the 1D mean t* (dq/dt = 0 there, so t* is    */
+/* held fixed when differentiating q). Sigma^-1 = R S^-2 R^T with R the   */
+/* rotation of the normalised quaternion.                                */
+/*                                                                       */
+/* Exact blend (Eq. 3): dL/dalpha_i = T_i (c_i - B_i), B_i the blend of   */
+/* everything behind i including the background; dL/dc_i = T_i alpha_i.  */
+/* Stochastic estimate (one sample with closest accepted hit k, colour   */
+/* c_k or bg): dL/dc_k = 1, and for every valid i in front of k          */
+/* dL/dalpha_i = (c_i - c_k) / (1 - alpha_i). Both are unbiased for the  */
+/* blend gradient: i in front of k means i and its prefix were rejected, */
+/* probability T_i (1 - alpha_i), after which c_k has mean B_i.          */
+/* Discontinuities (order swaps, the ellipsoid cutoff) are not           */
+/* differentiated.                                                       */
+/* ------------------------------------------------------------------ */
+
+/* d alpha / d theta (11 entries) of Gaussian g for the ray (o, d). */
+static void dalpha_dtheta(const orc_scene *sc, const orc_gauss *G, int64_t g, const double o[3],
+                          const double d[3], double t, double alpha, double out[11])
+{
+    double v[3];
+    for (int k = 0; k < 3; ++k) v[k] = o[k] + t * d[k] - G->mu[k];
+    double Sv[3];
+    for (int i = 0; i < 3; ++i)
+        Sv[i] = G->Sinv[3 * i] * v[0] + G->Sinv[3 * i + 1] * v[1] + G->Sinv[3 * i + 2] * v[2];
+    const double dadq = -0.5 * alpha;
+    /* mean: dq/dmu = -2 Sigma^-1 v */
+    for (int k = 0; k < 3; ++k) out[k] = dadq * (-2.0 * Sv[k]);
+    /* rotation and scales */
+    double R[9];
+    quat_to_rot(sc->quats + 4 * g, R);
+    double a[3], inv_s2[3];
+    for (int k = 0; k < 3; ++k) {
+        a[k] = R[k] * v[0] + R[3 + k] * v[1] + R[6 + k] * v[2]; /* (R^T v)_k */
+        double s = exp((double)sc->log_scales[3 * g + k]);
+        inv_s2[k] = 1.0 / (s * s);
+        out[3 + k] = dadq * (-2.0 * a[k] * a[k] * inv_s2[k]);
+    }
+    /* dq/dR_jk = 2 v_j a_k / s_k^2 */
+    double dR[9];
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) dR[3 * j + k] = 2.0 * v[j] * a[k] * inv_s2[k];
+    const float *qf = sc->quats + 4 * g;
+    double qr[4] = {qf[0], qf[1], qf[2], qf[3]};
+    double n = sqrt(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
+    double w = qr[0] / n, x = qr[1] / n, y = qr[2] / n, z = qr[3] / n;
+    /* dR/dw, dR/dx, dR/dy, dR/dz of the rotation matrix of (w,x,y,z) */
+    const double Dw[9] = {0, -2 * z, 2 * y, 2 * z, 0, -2 * x, -2 * y, 2 * x, 0};
+    const double Dx[9] = {0, 2 * y, 2 * z, 2 * y, -4 * x, -2 * w, 2 * z, 2 * w, -4 * x};
+    const double Dy[9] = {-4 * y, 2 * x, 2 * w, 2 * x, 0, 2 * z, -2 * w, 2 * z, -4 * y};
+    const double Dz[9] = {-4 * z, -2 * w, 2 * x, 2 * w, -4 * z, 2 * y, 2 * x, 2 * y, 0};
+    const double *D[4] = {Dw, Dx, Dy, Dz};
+    double gq[4];
+    for (int c = 0; c < 4; ++c) {
+        double acc = 0.0;
+        for (int e = 0; e < 9; ++e) acc += dR[e] * D[c][e];
+        gq[c] = acc;
+    }
+    /* through the normalisation: (I - qhat qhat^T) / |q| */
+    double qh[4] = {w, x, y, z};
+    double dot = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+    for (int c = 0; c < 4; ++c) out[6 + c] = dadq * (gq[c] - dot * qh[c]) / n;
+    /* opacity logit */
+    out[10] = alpha * (1.0 - G->opacity);
+}
+
+typedef struct {
+    double *means, *log_scales, *quats, *logits, *sh;
+} orc_grads;
+
+static void add_theta(const orc_grads *gr, int64_t g, double scale, const double da[11])
+{
+    for (int k = 0; k < 3; ++k) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+        gr->means[3 * g + k] += scale * da[k];
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+        gr->log_scales[3 * g + k] += scale * da[3 + k];
+    }
+    for (int k = 0; k < 4; ++k) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+        gr->quats[4 * g + k] += scale * da[6 + k];
+    }
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+    gr->logits[g] += scale * da[10];
+}
+
+/* dc/dk for the colour of Gaussian g: w_ch * mask_ch * Y_K, accumulated. */
+static void add_sh(const orc_scene *sc, const orc_grads *gr, int64_t g, const double *Y,
+                   const double rgb_raw_pos[3], const double w[3])
+{
+    int K = (sc->sh_degree + 1) * (sc->sh_degree + 1);
+    for (int ch = 0; ch < 3; ++ch) {
+        if (!(rgb_raw_pos[ch] > 0.0)) continue; /* max(0, .) clamp */
+        for (int i = 0; i < K; ++i) {
+            double b = i == 0 ? 1.0 : Y[i];
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+            gr->sh[((size_t)g * K + i) * 3 + ch] += w[ch] * b;
+        }
+    }
+}
+
+/* Raw (unclamped) colour, to know which channels pass the clamp. */
+static void sh_raw(const orc_scene *sc, int64_t g, const double *Y, double raw[3])
+{
+    int K = (sc->sh_degree + 1) * (sc->sh_degree + 1);
+    const float *k = sc->sh + (size_t)g * K * 3;
+    for (int ch = 0; ch < 3; ++ch) {
+        double acc = (double)k[ch];
+        for (int i = 1; i < K; ++i) acc += Y[i] * (double)k[3 * i + ch];
+        raw[ch] = acc;
+    }
+}
+
+/* Exported: gradients of G = sum_p d_rgb[p] . L_p over the listed pixels.
+ * mode 0: exact blend (Eq. 3). mode 1: the stochastic estimator averaged
+ * over the spp * n_hits samples of each pixel, same draws as rendering.
+ * Gradient arrays (FP64, caller-zeroed, same layouts as the parameters)
+ * are accumulated. Returns the number of threads used. */
+int orc_grad_pinhole(const orc_scene *sc, const orc_pinhole *cam, const orc_params *p,
+                     int64_t n_pix, const int64_t *pix, const double *d_rgb, int mode,
+                     double *g_means, double *g_log_scales, double *g_quats, double *g_logits,
+                     double *g_sh, int n_threads)
+{
+    orc_gauss *act = activate_all(sc);
+    orc_grads gr = {g_means, g_log_scales, g_quats, g_logits, g_sh};
+    int64_t S = (int64_t)p->spp * p->n_hits;
+    int used = 1;
+#ifdef _OPENMP
+    if (n_threads <= 0) n_threads = omp_get_max_threads();
+#pragma omp parallel num_threads(n_threads)
+#endif
+    {
+#ifdef _OPENMP
+#pragma omp single
+        used = omp_get_num_threads();
+#endif
+        cand_list L = {0, 0, 0};
+        double *suffix = NULL;
+        int64_t suffix_cap = 0;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 2)
+#endif
+        for (int64_t r = 0; r < n_pix; ++r) {
+            int32_t x = (int32_t)(pix[r] % cam->width), y = (int32_t)(pix[r] / cam->width);
+            double o[3], d[3];
+            uint32_t rid;
+            orc_camera_ray(cam, x, y, o, d, &rid);
+            collect(sc, act, o, d, p->t_min, p->t_max, &L);
+            qsort(L.v, (size_t)L.n, sizeof(orc_cand), cand_cmp);
+            double Y[16];
+            orc_sh_basis(sc->sh_degree, d, Y);
+            const double *g = d_rgb + 3 * r;
+            if (mode == 0) {
+                if (L.n + 1 > suffix_cap) {
+                    suffix_cap = 2 * (L.n + 1);
+                    suffix = (double *)realloc(suffix, (size_t)suffix_cap * 3 * sizeof(double));
+                }
+                /* suffix[i] = blend of candidates i.. plus background */
+                for (int ch = 0; ch < 3; ++ch) suffix[3 * L.n + ch] = p->bg[ch];
+                for (int64_t i = L.n - 1; i >= 0; --i)
+                    for (int ch = 0; ch < 3; ++ch)
+                        suffix[3 * i + ch] = L.v[i].alpha * L.v[i].rgb[ch] +
+                                             (1.0 - L.v[i].alpha) * suffix[3 * (i + 1) + ch];
+                double T = 1.0;
+                for (int64_t i = 0; i < L.n; ++i) {
+                    const orc_cand *c = &L.v[i];
+                    double dG = 0.0;
+                    for (int ch = 0; ch < 3; ++ch)
+                        dG += g[ch] * (c->rgb[ch] - suffix[3 * (i + 1) + ch]);
+                    dG *= T;
+                    double da[11];
+                    dalpha_dtheta(sc, &act[c->gid], c->gid, o, d, c->t, c->alpha, da);
+                    add_theta(&gr, c->gid, dG, da);
+                    double raw[3], w[3];
+                    sh_raw(sc, c->gid, Y, raw);
+                    for (int ch = 0; ch < 3; ++ch) w[ch] = T * c->alpha * g[ch];
+                    add_sh(sc, &gr, c->gid, Y, raw, w);
+                    T *= (1.0 - c->alpha);
+                }
+            } else {
+                for (int64_t s = 0; s < S; ++s) {
+                    int64_t win = -1;
+                    for (int64_t i = 0; i < L.n; ++i) {
+                        double xi = orc_xi(p->seed, rid, (uint32_t)L.v[i].gid, (uint32_t)s,
+                                           p->stream_tag);
+                        if (xi < L.v[i].alpha) { win = i; break; } /* sorted: first accepted */
+                    }
+                    const double *ck = win >= 0 ? L.v[win].rgb : p->bg;
+                    if (win >= 0) {
+                        double raw[3], w[3];
+                        sh_raw(sc, L.v[win].gid, Y, raw);
+                        for (int ch = 0; ch < 3; ++ch) w[ch] = g[ch] / (double)S;
+                        add_sh(sc, &gr, L.v[win].gid, Y, raw, w);
+                    }
+                    int64_t n_front = win >= 0 ? win : L.n;
+                    for (int64_t i = 0; i < n_front; ++i) {
+                        const orc_cand *c = &L.v[i];
+                        double dG = 0.0;
+                        for (int ch = 0; ch < 3; ++ch) dG += g[ch] * (c->rgb[ch] - ck[ch]);
+                        dG /= (double)S * (1.0 - c->alpha);
+                        double da[11];
+                        dalpha_dtheta(sc, &act[c->gid], c->gid, o, d, c->t, c->alpha, da);
+                        add_theta(&gr, c->gid, dG, da);
+                    }
+                }
+            }
+        }
+        free(L.v);
+        free(suffix);
+    }
+    free(act);
+    return used;
+}

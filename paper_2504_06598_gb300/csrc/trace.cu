@@ -318,21 +318,32 @@ __device__ __forceinline__ bool slab(const float *lo_hi, const float inv[3], con
 // once every lane's clip has passed it. Each lane runs Alg. 1 on exactly
 // the leaves its own ray reaches, so per-lane results are those of an
 // independent traversal.
+struct Counts {
+    unsigned long long nodes = 0;        // nodes entered by this lane's own ray
+    unsigned long long prims = 0;        // Gaussians tested by this lane
+    unsigned long long draws = 0;        // Philox calls
+    unsigned long long node_fetch = 0;   // node records fetched by the warp
+    unsigned long long prim_fetch = 0;   // Gaussian records fetched by the warp
+};
+
 template <int N, bool COUNT>
 __device__ __forceinline__ void traverse_packet(const TraceArgs &a, Ray<N> &r, int pass,
                                                 uint32_t *stack, float *stack_t, uint32_t &err,
-                                                unsigned long long &n_nodes,
-                                                unsigned long long &n_prims,
-                                                unsigned long long &n_draws) {
+                                                Counts &cnt) {
     const uint32_t kAll = 0xffffffffu;
+    const bool lane0 = (threadIdx.x & 31) == 0;
     int sp = 0;
     uint32_t node = 0, steps = 0;
+    bool active = r.t_far >= a.t_min;  // this lane's ray entered the node
     for (;;) {
         if (++steps > a.step_limit) {
             err |= kErrSteps;
             break;
         }
-        if (COUNT) ++n_nodes;
+        if (COUNT) {
+            cnt.nodes += active;
+            cnt.node_fetch += lane0;
+        }
         const float4 *np = reinterpret_cast<const float4 *>(a.nodes + node);
         const float4 b0 = __ldg(np), b1 = __ldg(np + 1), b2 = __ldg(np + 2);
         const uint4 cref = __ldg(reinterpret_cast<const uint4 *>(np + 3));
@@ -345,11 +356,16 @@ __device__ __forceinline__ void traverse_packet(const TraceArgs &a, Ray<N> &r, i
         if (leafL || leafR) {
             // Alg. 1 on the leaves this lane's ray reaches, nearer box first
             const bool swap = leafL && leafR && hR && (!hL || tR < tL);
+            if (COUNT) {
+                const unsigned wl = __ballot_sync(kAll, leafL && hL);
+                const unsigned wr = __ballot_sync(kAll, leafR && hR);
+                if (lane0) cnt.prim_fetch += (wl != 0u) + (wr != 0u);
+            }
             for (int li = 0; li < 2; ++li) {
                 const bool right = (li == 0) == swap;
                 if (!(right ? leafR : leafL) || !(right ? hR : hL)) continue;
-                if (COUNT) ++n_prims;
-                intersect<N, COUNT>(a, r, (right ? cref.y : cref.x) & ~kLeafBit, pass, n_draws);
+                if (COUNT) ++cnt.prims;
+                intersect<N, COUNT>(a, r, (right ? cref.y : cref.x) & ~kLeafBit, pass, cnt.draws);
             }
             if (leafL) hL = false;
             if (leafR) hR = false;
@@ -369,15 +385,18 @@ __device__ __forceinline__ void traverse_packet(const TraceArgs &a, Ray<N> &r, i
             stack_t[sp] = left_first ? (hR ? tR : INFINITY) : (hL ? tL : INFINITY);
             ++sp;
             node = left_first ? cref.x : cref.y;
+            active = left_first ? hL : hR;
             continue;
         }
-        if (mL) { node = cref.x; continue; }
-        if (mR) { node = cref.y; continue; }
+        if (mL) { node = cref.x; active = hL; continue; }
+        if (mR) { node = cref.y; active = hR; continue; }
         bool found = false;
         while (sp > 0) {
             --sp;
-            if (__any_sync(kAll, stack_t[sp] <= r.t_far)) {
+            const bool want = stack_t[sp] <= r.t_far;
+            if (__any_sync(kAll, want)) {
                 node = stack[sp];
+                active = want;
                 found = true;
                 break;
             }
@@ -399,7 +418,8 @@ __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
     uint32_t stack[kMaxStack];
     float stack_t[kMaxStack];
     uint32_t err = 0;
-    unsigned long long n_nodes = 0, n_prims = 0, n_draws = 0, n_shaded = 0, n_rays = 0;
+    Counts cnt;
+    unsigned long long n_shaded = 0, n_rays = 0;
     for (;;) {
         uint32_t tile = 0;
         if (lane == 0) tile = atomicAdd(a.work, 1u);
@@ -425,8 +445,7 @@ __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
             update_clip(r, a.t_max);
             if (!valid) r.t_far = -INFINITY;  // lanes off the image never hit
             if (a.n_nodes > 0)
-                traverse_packet<N, COUNT>(a, r, pass, stack, stack_t, err, n_nodes, n_prims,
-                                          n_draws);
+                traverse_packet<N, COUNT>(a, r, pass, stack, stack_t, err, cnt);
             if (valid) {
                 // shade each slot once (Eq. 6) and accumulate (Eq. 7)
                 float Y[16];
@@ -462,11 +481,13 @@ __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
     }
     if (err) atomicOr(a.status, err);
     if (COUNT) {
-        atomicAdd(a.counters + 0, n_nodes);
-        atomicAdd(a.counters + 1, n_prims);
-        atomicAdd(a.counters + 2, n_draws);
+        atomicAdd(a.counters + 0, cnt.nodes);
+        atomicAdd(a.counters + 1, cnt.prims);
+        atomicAdd(a.counters + 2, cnt.draws);
         atomicAdd(a.counters + 3, n_rays);
         atomicAdd(a.counters + 4, n_shaded);
+        atomicAdd(a.counters + 5, cnt.node_fetch);
+        atomicAdd(a.counters + 6, cnt.prim_fetch);
     }
 }
 

@@ -125,13 +125,15 @@ def test_counters_do_not_change_results(gs):
     cam = scenes.default_camera(64, 48)
     g = gs.Gaussians.from_cloud(cloud)
     bvh = gs.build_bvh(g)
-    cnt = torch.zeros(5, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(7, dtype=torch.int64, device="cuda")
     a = gs.trace_stochastic(bvh, g, cam, spp=3, n_hits=4, counters=cnt).cpu()
     b = gs.trace_stochastic(bvh, g, cam, spp=3, n_hits=4).cpu()
     bvh.sync_status()
     c = cnt.cpu().numpy()
     assert torch.equal(a, b)
     assert c[3] == 64 * 48 and c[0] > c[3] and c[1] > 0 and c[2] > 0 and c[4] > 0
+    # a warp fetches each node once for its 32 rays: fewer fetches than entries
+    assert 0 < c[5] < c[0] and 0 < c[6] <= c[1]
     bvh.free()
 
 
