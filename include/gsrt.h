@@ -202,6 +202,32 @@ gs_status gs_trace_stochastic(const gs_bvh *bvh, const gs_gaussians *g, const gs
                               const gs_trace_params *p, float *rgb_out, int32_t *hit_id_out,
                               float *hit_t_out, void *stream);
 
+/* Unbiased stochastic gradient of an image loss (the differentiable
+ * rendering extension named at the end of the paper, Sec. 6). For each
+ * sample with closest accepted hit k (colour c_k, or bg):
+ *   dLoss/dc_k += g,  dLoss/dalpha_i += g . (c_i - c_k) / (1 - alpha_i)
+ * for every valid Gaussian i in front of k, with g = d_rgb / (spp*n_hits);
+ * alpha's dependence on the mean, log-scales, quaternion and opacity logit,
+ * and the colour's on the SH coefficients, are then chained through. The
+ * expectation is the gradient of the sorted blend of Eq. 3 (depth-order
+ * swaps and the ellipsoid cutoff are not differentiated). Hits are
+ * recomputed with the same keys as gs_trace_stochastic(bvh, g, cam, p), so
+ * the samples are the ones that trace rendered; no per-ray list is stored.
+ *   d_rgb            device float[height][width][3], dLoss/d(rgb_out)
+ *   d_means          device float[M][3]     } gradients, ACCUMULATED (+=),
+ *   d_log_scales     device float[M][3]     } float32 whatever sh_dtype is;
+ *   d_quats          device float[M][4]     } the caller zeroes them
+ *   d_opacity_logits device float[M]        }
+ *   d_sh             device float[M][K][3]  }
+ * quats must be 16-byte aligned. Accumulation uses atomics, so the summation
+ * order, and the last bits of the gradients, vary from run to run. Shares
+ * the handle's tile counter with gs_trace_stochastic: order the calls on one
+ * stream. */
+gs_status gs_trace_backward(const gs_bvh *bvh, const gs_gaussians *g, const gs_pinhole *cam,
+                            const gs_trace_params *p, const float *d_rgb, float *d_means,
+                            float *d_log_scales, float *d_quats, float *d_opacity_logits,
+                            float *d_sh, void *stream);
+
 /* Allocation-free variant of gs_build_bvh. The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- for
  * example a renderer thread that must never trigger the implicit device

@@ -76,6 +76,9 @@ _SIGNATURES = {
     "gs_bvh_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gs_trace_stochastic": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_trace_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_void_p]),
     "gs_build_bvh_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p]),
     "gs_status_string": (C.c_char_p, [C.c_int]),
@@ -273,6 +276,64 @@ def trace_stochastic(bvh: Bvh, g: Gaussians, cam, seed=0, spp=1, n_hits=1, t_min
     if want_hits:
         return rgb, hit_id, hit_t
     return rgb
+
+
+def trace_backward(bvh: Bvh, g: Gaussians, cam, d_rgb, seed=0, spp=1, n_hits=1, t_min=0.0,
+                   t_max=float("inf"), bg=(0.0, 0.0, 0.0), stack_depth=0, stream_tag=0,
+                   grads=None, stream=None):
+    """``gs_trace_backward``: stochastic gradients of sum(d_rgb * rgb).
+
+    Returns (and accumulates into, if given) a dict of float32 gradients
+    shaped like the parameters."""
+    cam = cam if isinstance(cam, Camera) else Camera.of(cam)
+    dev = g.means.device
+    if grads is None:
+        grads = {"means": torch.zeros_like(g.means), "log_scales": torch.zeros_like(g.log_scales),
+                 "quats": torch.zeros_like(g.quats),
+                 "opacity_logits": torch.zeros_like(g.opacity_logits),
+                 "sh": torch.zeros(g.sh.shape, dtype=torch.float32, device=dev)}
+    d_rgb = d_rgb.to(device=dev, dtype=torch.float32).contiguous()
+    gs_ = g.struct()
+    cs = cam.struct()
+    ps = _params(seed, spp, n_hits, t_min, t_max, bg, stack_depth, stream_tag, None)
+    _check(lib().gs_trace_backward(
+        bvh.handle, C.byref(gs_), C.byref(cs), C.byref(ps), C.c_void_p(d_rgb.data_ptr()),
+        C.c_void_p(grads["means"].data_ptr()), C.c_void_p(grads["log_scales"].data_ptr()),
+        C.c_void_p(grads["quats"].data_ptr()), C.c_void_p(grads["opacity_logits"].data_ptr()),
+        C.c_void_p(grads["sh"].data_ptr()), _stream_handle(stream)))
+    return grads
+
+
+class StochasticRender(torch.autograd.Function):
+    """Differentiable stochastic rendering of one view.
+
+    forward(means, log_scales, quats, opacity_logits, sh, sh_degree, cam,
+    options) -> rgb [H, W, 3]; backward returns the unbiased stochastic
+    gradients of gs_trace_backward (same seed, same samples)."""
+
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, sh_degree, cam, options):
+        g = Gaussians(means.detach(), log_scales.detach(), quats.detach(),
+                      opacity_logits.detach(), sh.detach(), sh_degree)
+        bvh = build_bvh(g)
+        rgb = trace_stochastic(bvh, g, cam, **options)
+        ctx.state = (bvh, g, cam, options)
+        return rgb
+
+    @staticmethod
+    def backward(ctx, d_rgb):
+        bvh, g, cam, options = ctx.state
+        grads = trace_backward(bvh, g, cam, d_rgb, **options)
+        bvh.free()
+        ctx.state = None
+        return (grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logits"],
+                grads["sh"].to(g.sh.dtype), None, None, None)
+
+
+def render_differentiable(means, log_scales, quats, opacity_logits, sh, sh_degree, cam, **options):
+    """Autograd entry point: rgb = StochasticRender.apply(...)."""
+    return StochasticRender.apply(means, log_scales, quats, opacity_logits, sh, sh_degree, cam,
+                                  options)
 
 
 def render(g: Gaussians, cam, stream=None, **kw):

@@ -233,16 +233,15 @@ gs_status gs_bvh_export(const gs_bvh *b, void *nodes_out, void *prims_out, uint6
     return GS_OK;
 }
 
-gs_status gs_trace_stochastic(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
-                              const gs_trace_params *p, float *rgb_out, int32_t *hit_id_out,
-                              float *hit_t_out, void *stream) {
+static gs_status check_trace_args(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
+                                  const gs_trace_params *p) {
     if (!b) return fail(GS_ERR_INVALID_ARG, "bvh is NULL");
     gs_status st = check_gaussians_host(g, true);
     if (st != GS_OK) return st;
     if (g->M != b->M)
         return fail(GS_ERR_INVALID_ARG, "gaussians M=%lld differs from the hierarchy's M=%lld",
                     (long long)g->M, (long long)b->M);
-    if (!cam || !p || !rgb_out) return fail(GS_ERR_INVALID_ARG, "cam, params or rgb_out is NULL");
+    if (!cam || !p) return fail(GS_ERR_INVALID_ARG, "cam or params is NULL");
     if (cam->width < 1 || cam->height < 1 || cam->width > 65536 || cam->height > 65536)
         return fail(GS_ERR_INVALID_ARG, "image size %dx%d out of range", cam->width, cam->height);
     if ((uint64_t)cam->ray_id_offset + (uint64_t)cam->width * (uint64_t)cam->height >
@@ -263,6 +262,15 @@ gs_status gs_trace_stochastic(const gs_bvh *b, const gs_gaussians *g, const gs_p
     if (p->depth_mode != 0) return fail(GS_ERR_INVALID_ARG, "depth_mode=%d unsupported", p->depth_mode);
     if (isnan(p->t_min) || isnan(p->t_max) || !(p->t_min < p->t_max))
         return fail(GS_ERR_INVALID_ARG, "need t_min < t_max");
+    return GS_OK;
+}
+
+gs_status gs_trace_stochastic(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
+                              const gs_trace_params *p, float *rgb_out, int32_t *hit_id_out,
+                              float *hit_t_out, void *stream) {
+    gs_status st = check_trace_args(b, g, cam, p);
+    if (st != GS_OK) return st;
+    if (!rgb_out) return fail(GS_ERR_INVALID_ARG, "rgb_out is NULL");
     if ((hit_id_out == nullptr) != (hit_t_out == nullptr))
         return fail(GS_ERR_INVALID_ARG, "hit_id_out and hit_t_out go together");
     if ((st = check_device()) != GS_OK) return st;
@@ -273,6 +281,26 @@ gs_status gs_trace_stochastic(const gs_bvh *b, const gs_gaussians *g, const gs_p
     if (p->counters && !is_device_ptr(p->counters))
         return fail(GS_ERR_INVALID_ARG, "counters is not a device pointer");
     return launch_trace(b, g, cam, p, rgb_out, hit_id_out, hit_t_out, (cudaStream_t)stream);
+}
+
+gs_status gs_trace_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
+                            const gs_trace_params *p, const float *d_rgb, float *d_means,
+                            float *d_log_scales, float *d_quats, float *d_opacity_logits,
+                            float *d_sh, void *stream) {
+    gs_status st = check_trace_args(b, g, cam, p);
+    if (st != GS_OK) return st;
+    if (!d_rgb || !d_means || !d_log_scales || !d_quats || !d_opacity_logits || !d_sh)
+        return fail(GS_ERR_INVALID_ARG, "d_rgb and every gradient array are required");
+    if (((uintptr_t)g->quats & 15u) != 0)
+        return fail(GS_ERR_INVALID_ARG, "quats must be 16-byte aligned");
+    if ((st = check_device()) != GS_OK) return st;
+    if ((st = check_gaussians_device(g, true)) != GS_OK) return st;
+    const void *ptrs[6] = {d_rgb, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh};
+    for (const void *q : ptrs)
+        if (!is_device_ptr(q)) return fail(GS_ERR_INVALID_ARG, "gradient arrays must be device pointers");
+    if (b->M == 0) return GS_OK;
+    return launch_backward(b, g, cam, p, d_rgb, d_means, d_log_scales, d_quats, d_opacity_logits,
+                           d_sh, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -1,0 +1,404 @@
+// backward.cu -- unbiased stochastic gradients of an image loss (the
+// differentiable-rendering extension the paper names in Sec. 6).
+//
+// For one sample whose closest accepted hit is k (colour c_k, or the
+// background when nothing was accepted), with g = dLoss/dpixel / S:
+//   dc_k          += g                      (colour of the selected hit)
+//   dalpha_i      += g . (c_i - c_k) / (1 - alpha_i)
+//                    for every valid Gaussian i in front of k in (t, id)
+//                    order; those are exactly the ones the sample rejected.
+// Both are unbiased for the gradient of the sorted blend of Eq. 3, whose
+// dL/dalpha_i = T_i (c_i - B_i) and dL/dc_i = T_i alpha_i. Order swaps and
+// the ellipsoid cutoff are not differentiated.
+//
+// Nothing is stored between the forward and backward passes: each pass
+// re-runs the forward traversal with the same keys (identical winners),
+// then a second traversal clipped at the winners' depths enumerates the
+// Gaussians in front of them. Gradients are accumulated with atomics,
+// reduced across the warp first for the warp's shared leaf.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "trace_common.cuh"
+
+namespace gsrt {
+namespace {
+
+// One candidate evaluated without acceptance, by the same formulas as
+// intersect(): base point, 1D mean, and the local coordinates of the point
+// on the ray at the mean.
+struct Cand {
+    float t, tc, tau, q, alpha, opacity;
+    float v[3];  // x* - mu, world
+    float u[3];  // M v = S^-1 R_q^T v
+    float m[9];
+    uint32_t gid;
+    bool valid;
+};
+
+__device__ __forceinline__ Cand eval_cand(const TraceArgs &a, const float o[3], const float d[3],
+                                          uint32_t idx) {
+    Cand c;
+    const float4 *pp = reinterpret_cast<const float4 *>(a.prims + idx);
+    const float4 p0 = __ldg(pp), p1 = __ldg(pp + 1), p2 = __ldg(pp + 2), p3 = __ldg(pp + 3);
+    const float mu[3] = {p0.x, p0.y, p0.z};
+    const float m[9] = {p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w, p3.x};
+    c.gid = __float_as_uint(p3.y);
+    c.opacity = p0.w;
+    float h[3], l[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float s = o[i] - mu[i];
+        const float bp = s - o[i];
+        const float ap = s - bp;
+        l[i] = (o[i] - ap) + (-mu[i] - bp);
+        h[i] = s;
+    }
+    const float tc = -fmaf(h[0], d[0], fmaf(h[1], d[1], h[2] * d[2]));
+    float w[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) w[i] = fmaf(tc, d[i], h[i]) + l[i];
+    float md[3], mw[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        md[i] = fmaf(m[3 * i], d[0], fmaf(m[3 * i + 1], d[1], m[3 * i + 2] * d[2]));
+        mw[i] = fmaf(m[3 * i], w[0], fmaf(m[3 * i + 1], w[1], m[3 * i + 2] * w[2]));
+    }
+    const float dd = fmaf(md[0], md[0], fmaf(md[1], md[1], md[2] * md[2]));
+    const float wd = fmaf(mw[0], md[0], fmaf(mw[1], md[1], mw[2] * md[2]));
+    const float inv_dd = 1.0f / dd;
+    const float tau = -wd * inv_dd;
+    const float t = tc + tau;
+    float w2[3], mw2[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) w2[i] = fmaf(tau, d[i], w[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        mw2[i] = fmaf(m[3 * i], w2[0], fmaf(m[3 * i + 1], w2[1], m[3 * i + 2] * w2[2]));
+    const float ww = fmaf(mw2[0], mw2[0], fmaf(mw2[1], mw2[1], mw2[2] * mw2[2]));
+    const float wd2 = fmaf(mw2[0], md[0], fmaf(mw2[1], md[1], mw2[2] * md[2]));
+    const float q = fmaxf(ww - wd2 * wd2 * inv_dd, 0.0f);
+    c.t = t;
+    c.tc = tc;
+    c.tau = tau;
+    c.q = q;
+    c.alpha = p0.w * expf(-0.5f * q);
+    for (int i = 0; i < 3; ++i) {
+        c.v[i] = w2[i];
+        c.u[i] = mw2[i];
+    }
+    for (int i = 0; i < 9; ++i) c.m[i] = m[i];
+    c.valid = (t > a.t_min) && (t < a.t_max) && (q <= kS2);
+    return c;
+}
+
+// d alpha / d(mu, log s, quat, logit) of one candidate; alpha = o exp(-q/2),
+// q = |u|^2 with u = S^-1 R_q^T v, and t held at the 1D mean (dq/dt = 0).
+__device__ void grad_alpha(const TraceArgs &a, const Cand &c, float out[11]) {
+    const float dadq = -0.5f * c.alpha;
+    // mean: dq/dmu = -2 M^T u
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        out[j] = dadq * -2.0f * fmaf(c.m[j], c.u[0], fmaf(c.m[3 + j], c.u[1], c.m[6 + j] * c.u[2]));
+    // log-scales: dq/dlog s_k = -2 u_k^2
+    float inv_s[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        out[3 + k] = dadq * -2.0f * c.u[k] * c.u[k];
+        inv_s[k] = expf(-__ldg(a.log_scales + 3 * (int64_t)c.gid + k));
+    }
+    // rotation: dq/dR_jk = 2 v_j u_k / s_k, then R(q) and the normalisation
+    float dR[9];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dR[3 * j + k] = 2.0f * c.v[j] * c.u[k] * inv_s[k];
+    const float4 qr = __ldg(reinterpret_cast<const float4 *>(a.quats) + c.gid);
+    const float n = sqrtf(qr.x * qr.x + qr.y * qr.y + qr.z * qr.z + qr.w * qr.w);
+    const float w = qr.x / n, x = qr.y / n, y = qr.z / n, z = qr.w / n;
+    const float Dw[9] = {0.0f, -2 * z, 2 * y, 2 * z, 0.0f, -2 * x, -2 * y, 2 * x, 0.0f};
+    const float Dx[9] = {0.0f, 2 * y, 2 * z, 2 * y, -4 * x, -2 * w, 2 * z, 2 * w, -4 * x};
+    const float Dy[9] = {-4 * y, 2 * x, 2 * w, 2 * x, 0.0f, 2 * z, -2 * w, 2 * z, -4 * y};
+    const float Dz[9] = {-4 * z, -2 * w, 2 * x, 2 * w, -4 * z, 2 * y, 2 * x, 2 * y, 0.0f};
+    float gq[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        gq[0] = fmaf(dR[e], Dw[e], gq[0]);
+        gq[1] = fmaf(dR[e], Dx[e], gq[1]);
+        gq[2] = fmaf(dR[e], Dy[e], gq[2]);
+        gq[3] = fmaf(dR[e], Dz[e], gq[3]);
+    }
+    const float qh[4] = {w, x, y, z};
+    const float dot = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[6 + k] = dadq * (gq[k] - dot * qh[k]) / n;
+    out[10] = c.alpha * (1.0f - c.opacity);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Gradient of the leaf shared by the warp (same Gaussian for every lane
+// that reaches it): each lane forms its contribution, the warp sums them,
+// one lane adds the sums.
+template <int N>
+__device__ __forceinline__ void leaf_gradient(const TraceArgs &a, const Ray<N> &r, bool hit,
+                                              uint32_t idx, const float ck[N][3], const float g[3],
+                                              const float Y[16]) {
+    const uint32_t kAll = 0xffffffffu;
+    float contrib[11];
+#pragma unroll
+    for (int j = 0; j < 11; ++j) contrib[j] = 0.0f;
+    uint32_t gid = 0;
+    bool nz = false;
+    if (hit) {
+        const Cand c = eval_cand(a, r.o, r.d, idx);
+        gid = c.gid;
+        if (c.valid) {
+            float coef = 0.0f;
+            bool any = false;
+            float ci[3];
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                if (!lex_closer(c.tc, c.tau, c.gid, r.slot[k])) continue;
+                if (!any) {
+                    sh_colour(a, c.gid, Y, ci);
+                    any = true;
+                }
+                coef += g[0] * (ci[0] - ck[k][0]) + g[1] * (ci[1] - ck[k][1]) +
+                        g[2] * (ci[2] - ck[k][2]);
+            }
+            if (any && coef != 0.0f) {
+                // a rejected hit has alpha <= xi < 1
+                coef /= (1.0f - c.alpha);
+                grad_alpha(a, c, contrib);
+#pragma unroll
+                for (int j = 0; j < 11; ++j) contrib[j] *= coef;
+                nz = true;
+            }
+        }
+    }
+    const unsigned m = __ballot_sync(kAll, nz);
+    if (!m) return;
+    const int leader = __ffs(m) - 1;
+    gid = __shfl_sync(kAll, gid, leader);
+    float sum[11];
+#pragma unroll
+    for (int j = 0; j < 11; ++j) sum[j] = warp_sum(contrib[j]);
+    if ((int)(threadIdx.x & 31) == leader) {
+        const int64_t gg = gid;
+        for (int k = 0; k < 3; ++k) {
+            atomicAdd(a.g_means + 3 * gg + k, sum[k]);
+            atomicAdd(a.g_log_scales + 3 * gg + k, sum[3 + k]);
+        }
+        for (int k = 0; k < 4; ++k) atomicAdd(a.g_quats + 4 * gg + k, sum[6 + k]);
+        atomicAdd(a.g_logits + gg, sum[10]);
+    }
+}
+
+// Second traversal of a pass: every leaf the lane's ray reaches before its
+// farthest slot (no acceptance, no clipping), in packet order.
+template <int N>
+__device__ void enumerate_packet(const TraceArgs &a, const Ray<N> &r, const float ck[N][3],
+                                 const float g[3], const float Y[16], uint32_t *stack,
+                                 float *stack_t, uint32_t &err) {
+    const uint32_t kAll = 0xffffffffu;
+    int sp = 0;
+    uint32_t node = 0, steps = 0;
+    for (;;) {
+        if (++steps > a.step_limit) {
+            err |= kErrSteps;
+            break;
+        }
+        const float4 *np = reinterpret_cast<const float4 *>(a.nodes + node);
+        const float4 b0 = __ldg(np), b1 = __ldg(np + 1), b2 = __ldg(np + 2);
+        const uint4 cref = __ldg(reinterpret_cast<const uint4 *>(np + 3));
+        const float boxL[6] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
+        const float boxR[6] = {b1.z, b1.w, b2.x, b2.y, b2.z, b2.w};
+        float tL, tR;
+        bool hL = slab(boxL, r.inv, r.oinv, a.t_min, r.t_far, tL);
+        bool hR = slab(boxR, r.inv, r.oinv, a.t_min, r.t_far, tR);
+        if (cref.x & kLeafBit) {
+            leaf_gradient<N>(a, r, hL, cref.x & ~kLeafBit, ck, g, Y);
+            hL = false;
+        }
+        if (cref.y & kLeafBit) {
+            leaf_gradient<N>(a, r, hR, cref.y & ~kLeafBit, ck, g, Y);
+            hR = false;
+        }
+        const unsigned mL = __ballot_sync(kAll, hL), mR = __ballot_sync(kAll, hR);
+        if (mL && mR) {
+            const unsigned lf = __ballot_sync(kAll, hL && (!hR || tL <= tR));
+            const bool left_first = 2 * __popc(lf) >= __popc(mL | mR);
+            if (sp >= a.stack_depth) {
+                err |= kErrStack;
+                break;
+            }
+            stack[sp] = left_first ? cref.y : cref.x;
+            stack_t[sp] = left_first ? (hR ? tR : INFINITY) : (hL ? tL : INFINITY);
+            ++sp;
+            node = left_first ? cref.x : cref.y;
+            continue;
+        }
+        if (mL) { node = cref.x; continue; }
+        if (mR) { node = cref.y; continue; }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (__any_sync(kAll, stack_t[sp] <= r.t_far)) {
+                node = stack[sp];
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_backward(const TraceArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t kAll = 0xffffffffu;
+    const uint32_t tiles_x = (a.width + 7) / 8, tiles_y = (a.height + 3) / 4;
+    const uint32_t n_tiles = tiles_x * tiles_y;
+    const int K = (a.sh_degree + 1) * (a.sh_degree + 1);
+    uint32_t stack[kMaxStack];
+    float stack_t[kMaxStack];
+    uint32_t err = 0;
+    Counts cnt;
+    for (;;) {
+        uint32_t tile = 0;
+        if (lane == 0) tile = atomicAdd(a.work, 1u);
+        tile = __shfl_sync(kAll, tile, 0);
+        if (tile >= n_tiles) break;
+        const int x = (int)((tile % tiles_x) * 8 + (lane & 7));
+        const int y = (int)((tile / tiles_x) * 4 + (lane >> 3));
+        const bool valid = x < a.width && y < a.height;
+        const int64_t pix = valid ? (int64_t)y * a.width + x : 0;
+        Ray<N> r;
+        camera_ray(a, valid ? x : 0, valid ? y : 0, r.d);
+        for (int i = 0; i < 3; ++i) {
+            r.o[i] = a.eye[i];
+            const float di = fabsf(r.d[i]) < 1e-30f ? copysignf(1e-30f, r.d[i]) : r.d[i];
+            r.inv[i] = 1.0f / di;
+            r.oinv[i] = r.o[i] * r.inv[i];
+        }
+        r.ray_id = a.ray_id_offset + (uint32_t)pix;
+        float Y[16];
+        sh_basis(a.sh_degree, r.d, Y);
+        const float inv_s = 1.0f / (float)((int64_t)a.spp * N);
+        float g[3] = {0.0f, 0.0f, 0.0f};
+        if (valid)
+            for (int ch = 0; ch < 3; ++ch) g[ch] = a.d_rgb[3 * pix + ch] * inv_s;
+        for (int pass = 0; pass < a.spp; ++pass) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) r.slot[k] = Slot{INFINITY, INFINITY, 0.0f, 0xffffffffu};
+            update_clip(r, a.t_max);
+            if (!valid) r.t_far = -INFINITY;
+            if (a.n_nodes == 0) continue;
+            // 1) the forward traversal: same keys, same winners
+            traverse_packet<N, false>(a, r, pass, stack, stack_t, err, cnt);
+            // 2) colours of the winners; dLoss/dk of the selected Gaussians
+            float ck[N][3];
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                if (valid && r.slot[k].gid != 0xffffffffu) {
+                    float raw[3];
+                    sh_colour_raw(a, r.slot[k].gid, Y, raw);
+                    const int64_t base = (int64_t)r.slot[k].gid * K * 3;
+                    for (int ch = 0; ch < 3; ++ch) {
+                        ck[k][ch] = fmaxf(raw[ch], 0.0f);
+                        if (raw[ch] > 0.0f && g[ch] != 0.0f)
+                            for (int i = 0; i < K; ++i)
+                                atomicAdd(a.g_sh + base + 3 * i + ch, g[ch] * Y[i]);
+                    }
+                } else {
+                    for (int ch = 0; ch < 3; ++ch) ck[k][ch] = a.bg[ch];
+                }
+            }
+            // 3) every Gaussian in front of a winner
+            update_clip(r, a.t_max);
+            if (!valid) r.t_far = -INFINITY;
+            enumerate_packet<N>(a, r, ck, g, Y, stack, stack_t, err);
+            __syncwarp();
+        }
+    }
+    if (err) atomicOr(a.status, err);
+}
+
+template <int N>
+gs_status launch_backward_n(const TraceArgs &a, cudaStream_t s) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_backward<N>, kThreads, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "backward launch setup");
+    const uint32_t tiles = (uint32_t)(((a.width + 7) / 8) * ((a.height + 3) / 4));
+    uint32_t blocks = (uint32_t)sms * (uint32_t)(per > 0 ? per : 1);
+    const uint32_t max_blocks = (tiles + kThreads / 32 - 1) / (kThreads / 32);
+    if (blocks > max_blocks) blocks = max_blocks;
+    if ((e = cudaMemsetAsync(a.work, 0, sizeof(uint32_t), s)) != cudaSuccess)
+        return cuda_fail(e, "reset work counter");
+    k_backward<N><<<blocks, kThreads, 0, s>>>(a);
+    return GS_OK;
+}
+
+}  // namespace
+
+gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
+                          const gs_trace_params *p, const float *d_rgb, float *d_means,
+                          float *d_log_scales, float *d_quats, float *d_logits, float *d_sh,
+                          cudaStream_t s) {
+    TraceArgs a = {};
+    a.nodes = b->nodes;
+    a.prims = b->prims;
+    a.sh = g->sh;
+    a.n_nodes = b->n_nodes;
+    a.sh_degree = g->sh_degree;
+    a.sh_dtype = g->sh_dtype;
+    a.width = cam->width;
+    a.height = cam->height;
+    a.ray_id_offset = cam->ray_id_offset;
+    for (int i = 0; i < 3; ++i) {
+        a.eye[i] = cam->eye[i];
+        a.look_at[i] = cam->look_at[i];
+        a.up[i] = cam->up[i];
+        a.bg[i] = p->bg[i];
+    }
+    a.tan_half = (float)tan((double)cam->fov_y_deg * 3.14159265358979323846 / 360.0);
+    a.key0 = (uint32_t)(p->seed & 0xffffffffu);
+    a.key1 = (uint32_t)(p->seed >> 32);
+    a.stream_tag = p->stream_tag;
+    a.spp = p->spp;
+    a.t_min = p->t_min;
+    a.t_max = p->t_max;
+    a.stack_depth = p->stack_depth == 0 ? kMaxStack : p->stack_depth;
+    a.step_limit = (uint32_t)(b->n_nodes + 8 < (int64_t)kStepLimit ? b->n_nodes + 8 : kStepLimit);
+    a.status = b->status;
+    a.work = b->status + 1;
+    a.d_rgb = d_rgb;
+    a.log_scales = g->log_scales;
+    a.quats = g->quats;
+    a.g_means = d_means;
+    a.g_log_scales = d_log_scales;
+    a.g_quats = d_quats;
+    a.g_logits = d_logits;
+    a.g_sh = d_sh;
+    gs_status st;
+    switch (p->n_hits) {
+        case 1: st = launch_backward_n<1>(a, s); break;
+        case 2: st = launch_backward_n<2>(a, s); break;
+        case 4: st = launch_backward_n<4>(a, s); break;
+        case 8: st = launch_backward_n<8>(a, s); break;
+        default: return fail(GS_ERR_INVALID_ARG, "n_hits must be 1, 2, 4 or 8");
+    }
+    if (st != GS_OK) return st;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+    return GS_OK;
+}
+
+}  // namespace gsrt

@@ -84,6 +84,12 @@ bool is_device_ptr(const void *p);
 gs_status build_into(gs_bvh *b, const gs_gaussians *g, cudaStream_t s);
 int64_t radix_tiles(int64_t n);
 
+// Backward (backward.cu)
+gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
+                          const gs_trace_params *p, const float *d_rgb, float *d_means,
+                          float *d_log_scales, float *d_quats, float *d_logits, float *d_sh,
+                          cudaStream_t s);
+
 // Trace (trace.cu)
 gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
                        const gs_trace_params *p, float *rgb, int32_t *hit_id, float *hit_t,

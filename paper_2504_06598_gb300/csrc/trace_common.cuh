@@ -1,0 +1,405 @@
+// trace_common.cuh -- device code shared by the forward trace (trace.cu)
+// and the backward pass (backward.cu): launch arguments, Philox, camera
+// rays, spherical harmonics, the Alg. 1 intersection routine, the slab test
+// and the warp packet traversal. Both translation units compile the same
+// source, so their per-candidate arithmetic is identical.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "gsrt_internal.cuh"
+
+namespace gsrt {
+namespace {
+
+constexpr int kThreads = 128;
+
+struct TraceArgs {
+    const Node *nodes;
+    const PrimRec *prims;
+    const void *sh;
+    int64_t n_nodes;
+    int sh_degree;
+    int sh_dtype;
+    int width, height;
+    uint32_t ray_id_offset;
+    float eye[3], look_at[3], up[3];
+    float tan_half;
+    uint32_t key0, key1, stream_tag;
+    int spp;
+    float t_min, t_max;
+    float bg[3];
+    int stack_depth;
+    uint32_t step_limit;
+    float *rgb;
+    int32_t *hit_id;
+    float *hit_t;
+    unsigned long long *counters;
+    uint32_t *status;
+    uint32_t *work;  // tile counter of the persistent launch
+    // backward pass only
+    const float *d_rgb;        // [H][W][3] dLoss/d(pixel mean)
+    const float *log_scales;   // raw parameters, for the scale and rotation
+    const float *quats;        // derivatives
+    float *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh;
+};
+
+// ---------------------------------------------------------------- Philox
+// Philox-4x32-10 (Salmon et al., SC'11): ten rounds, multipliers
+// 0xD2511F53 and 0xCD9E8D57, key increments 0x9E3779B9 and 0xBB67AE85.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ float lane_to_unit(uint32_t u) {
+    return (float)(u >> 8) * 0x1p-24f;
+}
+
+__device__ __forceinline__ uint32_t pick(const uint4 &v, int lane) {
+    return lane == 0 ? v.x : lane == 1 ? v.y : lane == 2 ? v.z : v.w;
+}
+
+// ---------------------------------------------------------------- camera
+// Float32 camera ray with every operation rounded once (no contraction).
+__device__ __forceinline__ void normalise_rn(float v[3]) {
+    float n2 = __fmul_rn(v[0], v[0]);
+    n2 = __fadd_rn(n2, __fmul_rn(v[1], v[1]));
+    n2 = __fadd_rn(n2, __fmul_rn(v[2], v[2]));
+    const float n = __fsqrt_rn(n2);
+    v[0] = __fdiv_rn(v[0], n);
+    v[1] = __fdiv_rn(v[1], n);
+    v[2] = __fdiv_rn(v[2], n);
+}
+
+__device__ __forceinline__ void cross_rn(const float a[3], const float b[3], float c[3]) {
+    c[0] = __fsub_rn(__fmul_rn(a[1], b[2]), __fmul_rn(a[2], b[1]));
+    c[1] = __fsub_rn(__fmul_rn(a[2], b[0]), __fmul_rn(a[0], b[2]));
+    c[2] = __fsub_rn(__fmul_rn(a[0], b[1]), __fmul_rn(a[1], b[0]));
+}
+
+__device__ __forceinline__ void camera_ray(const TraceArgs &a, int x, int y, float d[3]) {
+    float f[3], r[3], u[3];
+    for (int i = 0; i < 3; ++i) f[i] = __fsub_rn(a.look_at[i], a.eye[i]);
+    normalise_rn(f);
+    cross_rn(f, a.up, r);
+    normalise_rn(r);
+    cross_rn(r, f, u);
+    const float s = __fdiv_rn(a.tan_half, (float)a.height);
+    const float ux = __fmul_rn((float)(2 * x + 1 - a.width), s);
+    const float uy = __fmul_rn((float)(a.height - 1 - 2 * y), s);
+    for (int i = 0; i < 3; ++i)
+        d[i] = __fadd_rn(__fadd_rn(f[i], __fmul_rn(ux, r[i])), __fmul_rn(uy, u[i]));
+    normalise_rn(d);
+}
+
+// ---------------------------------------------------------------- SH colour
+__device__ __forceinline__ float load_coef(const void *sh, int dtype, int64_t i) {
+    if (dtype == GS_SH_F32) return __ldg(static_cast<const float *>(sh) + i);
+    const unsigned short raw = __ldg(static_cast<const unsigned short *>(sh) + i);
+    if (dtype == GS_SH_F16) return __half2float(__ushort_as_half(raw));
+    return __uint_as_float((uint32_t)raw << 16);  // bfloat16
+}
+
+// Real spherical harmonics with the Condon-Shortley phase as polynomials in
+// the unit direction (x, y, z); constants are the normalisations
+// sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!), times sqrt(2) for m != 0, times the
+// Legendre polynomial coefficients. The DC term is pre-multiplied (basis 1).
+__device__ void sh_basis(int deg, const float d[3], float Y[16]) {
+    const float x = d[0], y = d[1], z = d[2];
+    Y[0] = 1.0f;
+    if (deg < 1) return;
+    const float c1 = 0.48860251190291992f;  // sqrt(3/(4 pi))
+    Y[1] = -c1 * y;
+    Y[2] = c1 * z;
+    Y[3] = -c1 * x;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = 1.0925484305920792f * x * y;              // sqrt(15/(4 pi))
+    Y[5] = -1.0925484305920792f * y * z;
+    Y[6] = 0.31539156525252005f * (3.0f * zz - 1.0f);  // sqrt(5/(16 pi))
+    Y[7] = -1.0925484305920792f * x * z;
+    Y[8] = 0.54627421529603959f * (xx - yy);          // sqrt(15/(16 pi))
+    if (deg < 3) return;
+    Y[9] = -0.59004358992664352f * y * (3.0f * xx - yy);  // sqrt(35/(32 pi))
+    Y[10] = 2.8906114426405538f * x * y * z;               // sqrt(105/(4 pi))
+    Y[11] = -0.45704579946446572f * y * (5.0f * zz - 1.0f);  // sqrt(21/(32 pi))
+    Y[12] = 0.37317633259011540f * z * (5.0f * zz - 3.0f);   // sqrt(7/(16 pi))
+    Y[13] = -0.45704579946446572f * x * (5.0f * zz - 1.0f);
+    Y[14] = 1.4453057213202769f * z * (xx - yy);            // sqrt(105/(16 pi))
+    Y[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
+}
+
+// Unclamped colour k_0 + sum Y_lm k_lm per channel.
+__device__ __forceinline__ void sh_colour_raw(const TraceArgs &a, uint32_t gid, const float Y[16],
+                                              float c[3]) {
+    const int K = (a.sh_degree + 1) * (a.sh_degree + 1);
+    const int64_t base = (int64_t)gid * K * 3;
+    float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f;
+    if (a.sh_dtype == GS_SH_F32 && K == 16) {
+        const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(a.sh) + base);
+        float v[48];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            const float4 q = __ldg(p + i);
+            v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            acc0 = fmaf(Y[k], v[3 * k], acc0);
+            acc1 = fmaf(Y[k], v[3 * k + 1], acc1);
+            acc2 = fmaf(Y[k], v[3 * k + 2], acc2);
+        }
+    } else {
+        for (int k = 0; k < K; ++k) {
+            acc0 = fmaf(Y[k], load_coef(a.sh, a.sh_dtype, base + 3 * k), acc0);
+            acc1 = fmaf(Y[k], load_coef(a.sh, a.sh_dtype, base + 3 * k + 1), acc1);
+            acc2 = fmaf(Y[k], load_coef(a.sh, a.sh_dtype, base + 3 * k + 2), acc2);
+        }
+    }
+    c[0] = acc0;
+    c[1] = acc1;
+    c[2] = acc2;
+}
+
+// View-dependent colour, clamped at zero.
+__device__ __forceinline__ void sh_colour(const TraceArgs &a, uint32_t gid, const float Y[16],
+                                          float c[3]) {
+    sh_colour_raw(a, gid, Y, c);
+    c[0] = fmaxf(c[0], 0.0f);
+    c[1] = fmaxf(c[1], 0.0f);
+    c[2] = fmaxf(c[2], 0.0f);
+}
+
+// ---------------------------------------------------------------- slots
+struct Slot {
+    float t;    // tc + tau, rounded (used for range clipping and output)
+    float tc;   // base-point parameter
+    float tau;  // 1D mean relative to the base point
+    uint32_t gid;
+};
+
+// (tc_a + tau_a, gid_a) < (tc_b + tau_b, gid_b), with the depth difference
+// formed as (tc_a - tc_b) + (tau_a - tau_b).
+__device__ __forceinline__ bool lex_closer(float tc, float tau, uint32_t gid, const Slot &s) {
+    const float dt = (tc - s.tc) + (tau - s.tau);
+    return dt < 0.0f || (dt == 0.0f && gid < s.gid);
+}
+
+template <int N>
+struct Ray {
+    float o[3], d[3], inv[3], oinv[3];
+    uint32_t ray_id;
+    Slot slot[N];
+    float t_far;  // conservative traversal clip
+};
+
+template <int N>
+__device__ __forceinline__ void update_clip(Ray<N> &r, float t_max) {
+    float far = r.slot[0].t;
+#pragma unroll
+    for (int k = 1; k < N; ++k) far = fmaxf(far, r.slot[k].t);
+    far = fminf(far, t_max);
+    // expanded by 2^-19 relative so float32 slab rounding cannot cull a
+    // node holding a hit that is (in exact arithmetic) not behind the clip
+    r.t_far = far + fabsf(far) * 0x1p-19f;
+}
+
+// Alg. 1 for primitive record idx against all N slots of the current pass.
+template <int N, bool COUNT>
+__device__ __forceinline__ void intersect(const TraceArgs &a, Ray<N> &r, uint32_t idx, int pass,
+                                          unsigned long long &n_draws) {
+    const float4 *pp = reinterpret_cast<const float4 *>(a.prims + idx);
+    const float4 p0 = __ldg(pp), p1 = __ldg(pp + 1), p2 = __ldg(pp + 2), p3 = __ldg(pp + 3);
+    const float mu[3] = {p0.x, p0.y, p0.z};
+    const float m[9] = {p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w, p3.x};
+    const uint32_t gid = __float_as_uint(p3.y);
+    // o - mu = h + l exactly (two-sum)
+    float h[3], l[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float s = r.o[i] - mu[i];
+        const float bp = s - r.o[i];
+        const float ap = s - bp;
+        l[i] = (r.o[i] - ap) + (-mu[i] - bp);
+        h[i] = s;
+    }
+    const float tc = -fmaf(h[0], r.d[0], fmaf(h[1], r.d[1], h[2] * r.d[2]));
+    float w[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) w[i] = fmaf(tc, r.d[i], h[i]) + l[i];
+    float md[3], mw[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        md[i] = fmaf(m[3 * i], r.d[0], fmaf(m[3 * i + 1], r.d[1], m[3 * i + 2] * r.d[2]));
+        mw[i] = fmaf(m[3 * i], w[0], fmaf(m[3 * i + 1], w[1], m[3 * i + 2] * w[2]));
+    }
+    const float dd = fmaf(md[0], md[0], fmaf(md[1], md[1], md[2] * md[2]));
+    const float wd = fmaf(mw[0], md[0], fmaf(mw[1], md[1], mw[2] * md[2]));
+    const float inv_dd = 1.0f / dd;
+    const float tau = -wd * inv_dd;
+    const float t = tc + tau;
+    // Alg. 1 range test; t_far only prunes hits behind every slot
+    if (!(t > a.t_min) || !(t < a.t_max) || !(t <= r.t_far)) return;
+    bool closer[N];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        closer[k] = lex_closer(tc, tau, gid, r.slot[k]);
+        any |= closer[k];
+    }
+    if (!any) return;
+    // refine the base point to the 1D mean, then the ellipsoid test (Eq. 2)
+    float w2[3], mw2[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) w2[i] = fmaf(tau, r.d[i], w[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        mw2[i] = fmaf(m[3 * i], w2[0], fmaf(m[3 * i + 1], w2[1], m[3 * i + 2] * w2[2]));
+    const float ww = fmaf(mw2[0], mw2[0], fmaf(mw2[1], mw2[1], mw2[2] * mw2[2]));
+    const float wd2 = fmaf(mw2[0], md[0], fmaf(mw2[1], md[1], mw2[2] * md[2]));
+    const float q = fmaxf(ww - wd2 * wd2 * inv_dd, 0.0f);
+    if (!(q <= kS2)) return;
+    const float alpha = p0.w * expf(-0.5f * q);
+    // Eq. 4: one Philox call serves four consecutive samples
+    uint4 u0 = make_uint4(0, 0, 0, 0), u1 = make_uint4(0, 0, 0, 0);
+    const uint32_t s0 = (uint32_t)pass * N;
+    u0 = philox10(make_uint4(r.ray_id, gid, s0 >> 2, a.stream_tag), a.key0, a.key1);
+    if (N == 8) u1 = philox10(make_uint4(r.ray_id, gid, (s0 >> 2) + 1, a.stream_tag), a.key0, a.key1);
+    if (COUNT) n_draws += 1 + (N == 8);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        if (!closer[k]) continue;
+        const uint32_t s = s0 + k;
+        const uint32_t bits = (N == 8 && k >= 4) ? pick(u1, s & 3) : pick(u0, s & 3);
+        if (lane_to_unit(bits) < alpha) {
+            r.slot[k].t = t;
+            r.slot[k].tc = tc;
+            r.slot[k].tau = tau;
+            r.slot[k].gid = gid;
+        }
+    }
+    update_clip(r, a.t_max);
+}
+
+// Slab test of one child box against [t_min, t_far].
+__device__ __forceinline__ bool slab(const float *lo_hi, const float inv[3], const float oinv[3],
+                                     float t_min, float t_far, float &t_enter) {
+    const float tx0 = fmaf(lo_hi[0], inv[0], -oinv[0]), tx1 = fmaf(lo_hi[3], inv[0], -oinv[0]);
+    const float ty0 = fmaf(lo_hi[1], inv[1], -oinv[1]), ty1 = fmaf(lo_hi[4], inv[1], -oinv[1]);
+    const float tz0 = fmaf(lo_hi[2], inv[2], -oinv[2]), tz1 = fmaf(lo_hi[5], inv[2], -oinv[2]);
+    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), t_min));
+    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), t_far));
+    t_enter = tn;
+    return tn <= tf;
+}
+
+// Packet traversal of one 8x4 pixel tile by one warp (same pass for all
+// lanes). The warp visits the union of the nodes its lanes need: every node
+// is fetched once for the whole warp (one broadcast load), each lane
+// slab-tests the children against its own clipped range and keeps its own
+// slots, and the warp descends while any lane still needs a child. A lane's
+// stack entry remembers its own entry distance, so a popped node is skipped
+// once every lane's clip has passed it. Each lane runs Alg. 1 on exactly
+// the leaves its own ray reaches, so per-lane results are those of an
+// independent traversal.
+struct Counts {
+    unsigned long long nodes = 0;        // nodes entered by this lane's own ray
+    unsigned long long prims = 0;        // Gaussians tested by this lane
+    unsigned long long draws = 0;        // Philox calls
+    unsigned long long node_fetch = 0;   // node records fetched by the warp
+    unsigned long long prim_fetch = 0;   // Gaussian records fetched by the warp
+};
+
+template <int N, bool COUNT>
+__device__ __forceinline__ void traverse_packet(const TraceArgs &a, Ray<N> &r, int pass,
+                                                uint32_t *stack, float *stack_t, uint32_t &err,
+                                                Counts &cnt) {
+    const uint32_t kAll = 0xffffffffu;
+    const bool lane0 = (threadIdx.x & 31) == 0;
+    int sp = 0;
+    uint32_t node = 0, steps = 0;
+    bool active = r.t_far >= a.t_min;  // this lane's ray entered the node
+    for (;;) {
+        if (++steps > a.step_limit) {
+            err |= kErrSteps;
+            break;
+        }
+        if (COUNT) {
+            cnt.nodes += active;
+            cnt.node_fetch += lane0;
+        }
+        const float4 *np = reinterpret_cast<const float4 *>(a.nodes + node);
+        const float4 b0 = __ldg(np), b1 = __ldg(np + 1), b2 = __ldg(np + 2);
+        const uint4 cref = __ldg(reinterpret_cast<const uint4 *>(np + 3));
+        const float boxL[6] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
+        const float boxR[6] = {b1.z, b1.w, b2.x, b2.y, b2.z, b2.w};
+        float tL, tR;
+        bool hL = slab(boxL, r.inv, r.oinv, a.t_min, r.t_far, tL);
+        bool hR = slab(boxR, r.inv, r.oinv, a.t_min, r.t_far, tR);
+        const bool leafL = (cref.x & kLeafBit) != 0u, leafR = (cref.y & kLeafBit) != 0u;
+        if (leafL || leafR) {
+            // Alg. 1 on the leaves this lane's ray reaches, nearer box first
+            const bool swap = leafL && leafR && hR && (!hL || tR < tL);
+            if (COUNT) {
+                const unsigned wl = __ballot_sync(kAll, leafL && hL);
+                const unsigned wr = __ballot_sync(kAll, leafR && hR);
+                if (lane0) cnt.prim_fetch += (wl != 0u) + (wr != 0u);
+            }
+            for (int li = 0; li < 2; ++li) {
+                const bool right = (li == 0) == swap;
+                if (!(right ? leafR : leafL) || !(right ? hR : hL)) continue;
+                if (COUNT) ++cnt.prims;
+                intersect<N, COUNT>(a, r, (right ? cref.y : cref.x) & ~kLeafBit, pass, cnt.draws);
+            }
+            if (leafL) hL = false;
+            if (leafR) hR = false;
+            hL = hL && tL <= r.t_far;
+            hR = hR && tR <= r.t_far;
+        }
+        const unsigned mL = __ballot_sync(kAll, hL), mR = __ballot_sync(kAll, hR);
+        if (mL && mR) {
+            // the child most lanes enter first is visited first
+            const unsigned lf = __ballot_sync(kAll, hL && (!hR || tL <= tR));
+            const bool left_first = 2 * __popc(lf) >= __popc(mL | mR);
+            if (sp >= a.stack_depth) {
+                err |= kErrStack;
+                break;
+            }
+            stack[sp] = left_first ? cref.y : cref.x;
+            stack_t[sp] = left_first ? (hR ? tR : INFINITY) : (hL ? tL : INFINITY);
+            ++sp;
+            node = left_first ? cref.x : cref.y;
+            active = left_first ? hL : hR;
+            continue;
+        }
+        if (mL) { node = cref.x; active = hL; continue; }
+        if (mR) { node = cref.y; active = hR; continue; }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            const bool want = stack_t[sp] <= r.t_far;
+            if (__any_sync(kAll, want)) {
+                node = stack[sp];
+                active = want;
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+    }
+}
+
+}  // namespace
+}  // namespace gsrt
