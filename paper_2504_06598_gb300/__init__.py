@@ -313,25 +313,36 @@ class StochasticRender(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, means, log_scales, quats, opacity_logits, sh, sh_degree, cam, options):
+        options = dict(options)
+        shared = options.pop("bvh", None)
         g = Gaussians(means.detach(), log_scales.detach(), quats.detach(),
                       opacity_logits.detach(), sh.detach(), sh_degree)
-        bvh = build_bvh(g)
+        if shared is not None:
+            shared.rebuild(g)  # reuse the caller's handle: no allocation
+            bvh = shared
+        else:
+            bvh = build_bvh(g)
         rgb = trace_stochastic(bvh, g, cam, **options)
-        ctx.state = (bvh, g, cam, options)
+        ctx.state = (bvh, shared is None, g, cam, options)
         return rgb
 
     @staticmethod
     def backward(ctx, d_rgb):
-        bvh, g, cam, options = ctx.state
+        bvh, owned, g, cam, options = ctx.state
         grads = trace_backward(bvh, g, cam, d_rgb, **options)
-        bvh.free()
+        if owned:
+            bvh.free()
         ctx.state = None
         return (grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logits"],
                 grads["sh"].to(g.sh.dtype), None, None, None)
 
 
 def render_differentiable(means, log_scales, quats, opacity_logits, sh, sh_degree, cam, **options):
-    """Autograd entry point: rgb = StochasticRender.apply(...)."""
+    """Autograd entry point: rgb = StochasticRender.apply(...).
+
+    ``bvh=`` (optional) is a handle to rebuild in place instead of building
+    a new one per call; its backward must run before the next forward that
+    uses the same handle."""
     return StochasticRender.apply(means, log_scales, quats, opacity_logits, sh, sh_degree, cam,
                                   options)
 
