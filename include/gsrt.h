@@ -107,7 +107,7 @@ typedef struct gs_pinhole {
  *   t_min, t_max  valid ray range, candidates need t_min < t < t_max
  *   bg            background colour of samples with no accepted hit
  *   depth_mode    0: depth is the mean of the 1D Gaussian (Sec. 3.1)
- *   stack_depth   traversal stack entries per ray, 1..64 (0 = 64)
+ *   stack_depth   traversal stack entries per ray, 1..96 (0 = 96)
  *   stream_tag    fourth Philox counter word, separates ray streams
  *   counters      optional device uint64[7], incremented by the launch:
  *                 {nodes entered by each ray's own traversal, Gaussians
@@ -133,13 +133,29 @@ typedef struct gs_trace_params {
  * the device status word. */
 typedef struct gs_bvh gs_bvh;
 
+/* Node format the traversal reads (the binary tree is always built too).
+ *   GS_NODES_BINARY    64-byte binary nodes, FP32 child boxes
+ *   GS_NODES_WIDE4     128-byte 4-wide nodes, FP32 child boxes
+ *   GS_NODES_WIDE4_Q8  64-byte 4-wide nodes, child boxes quantised to 8 bits
+ *                      per plane with outward rounding (a decoded box always
+ *                      contains the FP32 box, so no hit is lost and every
+ *                      result equals the FP32 traversal's) */
+enum { GS_NODES_BINARY = 0, GS_NODES_WIDE4 = 1, GS_NODES_WIDE4_Q8 = 2 };
+
+typedef struct gs_build_options {
+    int32_t node_format; /* GS_NODES_* */
+    int32_t reserved[7]; /* zero */
+} gs_build_options;
+
 typedef struct gs_bvh_info {
     int64_t M;            /* Gaussians indexed */
-    int64_t n_nodes;      /* internal nodes (max(M-1, 1), 0 when M = 0) */
+    int64_t n_nodes;      /* internal binary nodes (max(M-1, 1), 0 when M = 0) */
     int64_t capacity;     /* largest M a rebuild can take without allocating */
     int64_t device_bytes; /* device memory held by the handle */
-    int32_t node_bytes;   /* bytes per node record */
+    int32_t node_bytes;   /* bytes per binary node record */
     int32_t prim_bytes;   /* bytes per Gaussian record */
+    int32_t node_format;  /* GS_NODES_* the traversal uses */
+    int32_t wide_node_bytes; /* bytes per wide node (0 for binary) */
 } gs_bvh_info;
 
 /* Build the hierarchy over the Gaussians' bounding boxes (Sec. 3.2; the box
@@ -154,6 +170,12 @@ typedef struct gs_bvh_info {
  * for bad sizes or pointers, GS_ERR_OOM / GS_ERR_CUDA / GS_ERR_NO_DEVICE on
  * CUDA failures. Non-finite parameters are reported by gs_bvh_sync_status. */
 gs_status gs_build_bvh(const gs_gaussians *g, gs_bvh **out, void *stream);
+
+/* gs_build_bvh with options (NULL = defaults: binary nodes). Same rules and
+ * errors as gs_build_bvh; an unknown node_format returns
+ * GS_ERR_INVALID_ARG. Rebuilds keep the handle's node format. */
+gs_status gs_build_bvh_ex(const gs_gaussians *g, const gs_build_options *opt, gs_bvh **out,
+                          void *stream);
 
 /* Rebuild an existing handle for new parameters with M <= capacity, with no
  * allocation (the usual per-frame call when Gaussians move). Same rules as
@@ -182,6 +204,14 @@ gs_status gs_bvh_sync_status(gs_bvh *bvh, void *stream);
  * internal node index; node 0 is the root. */
 gs_status gs_bvh_export(const gs_bvh *bvh, void *nodes_out, void *prims_out,
                         uint64_t *codes_out, uint32_t *order_out);
+
+/* Copy the wide nodes of a GS_NODES_WIDE4 or GS_NODES_WIDE4_Q8 handle to
+ * host memory (synchronous). *n_out receives the number of wide nodes; at
+ * most `capacity` of them are written to out (wide_node_bytes each), so a
+ * call with capacity 0 queries the count. Node 0 is the root; a child
+ * reference is a Gaussian record (bit 31 set), a wide node index, or
+ * 0xffffffff for an unused slot. */
+gs_status gs_bvh_export_wide(const gs_bvh *bvh, void *out, int64_t capacity, int64_t *n_out);
 
 /* Render one pinhole view by stochastic ray tracing (Alg. 1, Eq. 4-7).
  *   bvh        built from the same Gaussians `g` (unchanged since)

@@ -60,7 +60,16 @@ class _TraceParams(C.Structure):
 class _BvhInfo(C.Structure):
     _fields_ = [("M", C.c_int64), ("n_nodes", C.c_int64), ("capacity", C.c_int64),
                 ("device_bytes", C.c_int64), ("node_bytes", C.c_int32),
-                ("prim_bytes", C.c_int32)]
+                ("prim_bytes", C.c_int32), ("node_format", C.c_int32),
+                ("wide_node_bytes", C.c_int32)]
+
+
+class _BuildOptions(C.Structure):
+    _fields_ = [("node_format", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+NODES_BINARY, NODES_WIDE4, NODES_WIDE4_Q8 = 0, 1, 2
+NODE_FORMATS = {"binary": NODES_BINARY, "wide4": NODES_WIDE4, "wide4_q8": NODES_WIDE4_Q8}
 
 
 _lib = None
@@ -69,6 +78,8 @@ _lib_lock = threading.Lock()
 # Every function the header declares, with its ctypes signature.
 _SIGNATURES = {
     "gs_build_bvh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_build_bvh_ex": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_bvh_export_wide": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "gs_bvh_rebuild": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "gs_bvh_free": (C.c_int, [C.c_void_p]),
     "gs_bvh_get_info": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -228,6 +239,17 @@ class Bvh:
         _check(lib().gs_bvh_export(self._h, ptr(nodes), ptr(prims), ptr(codes), ptr(order)))
         return {"nodes": nodes, "prims": prims, "codes": codes, "order": order}
 
+    def export_wide(self) -> np.ndarray:
+        """Wide nodes as raw uint32 words [n, wide_node_bytes/4]."""
+        info = self.info()
+        n = C.c_int64(0)
+        _check(lib().gs_bvh_export_wide(self._h, None, 0, C.byref(n)))
+        out = np.zeros((n.value, info["wide_node_bytes"] // 4), np.uint32)
+        if n.value:
+            _check(lib().gs_bvh_export_wide(self._h, out.ctypes.data_as(C.c_void_p), n.value,
+                                            C.byref(n)))
+        return out
+
     def free(self):
         if self._h is not None and _lib is not None:
             lib().gs_bvh_free(self._h)
@@ -240,11 +262,19 @@ class Bvh:
             pass
 
 
-def build_bvh(g: Gaussians, stream=None) -> Bvh:
-    """``gs_build_bvh``: hierarchy over the Gaussians' bounding boxes."""
+def build_bvh(g: Gaussians, stream=None, node_format="binary") -> Bvh:
+    """``gs_build_bvh`` / ``gs_build_bvh_ex``: hierarchy over the Gaussians'
+    bounding boxes; ``node_format`` is "binary", "wide4" or "wide4_q8"."""
     h = C.c_void_p()
     gs = g.struct()
-    _check(lib().gs_build_bvh(C.byref(gs), C.byref(h), _stream_handle(stream)))
+    fmt = NODE_FORMATS[node_format] if isinstance(node_format, str) else int(node_format)
+    if fmt == NODES_BINARY:
+        _check(lib().gs_build_bvh(C.byref(gs), C.byref(h), _stream_handle(stream)))
+    else:
+        opt = _BuildOptions()
+        opt.node_format = fmt
+        _check(lib().gs_build_bvh_ex(C.byref(gs), C.byref(opt), C.byref(h),
+                                     _stream_handle(stream)))
     return Bvh(h, g.M)
 
 

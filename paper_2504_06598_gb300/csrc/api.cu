@@ -81,7 +81,8 @@ static gs_status check_gaussians_device(const gs_gaussians *g, bool need_sh) {
 static void release(gs_bvh *b) {
     if (!b) return;
     void *bufs[] = {b->nodes, b->prims, b->status, b->codes[0], b->codes[1], b->vals[0],
-                    b->vals[1], b->parent, b->arrive, b->aabb, b->bounds, b->hist};
+                    b->vals[1], b->parent, b->arrive, b->aabb, b->bounds, b->hist,
+                    b->scan_tmp, b->wide, b->depth, b->wmap};
     for (void *p : bufs)
         if (p) cudaFree(p);
     free(b);
@@ -110,7 +111,18 @@ const char *gs_status_string(gs_status s) {
 const char *gs_last_error(void) { return g_last_error; }
 
 gs_status gs_build_bvh(const gs_gaussians *g, gs_bvh **out, void *stream) {
+    return gs_build_bvh_ex(g, nullptr, out, stream);
+}
+
+gs_status gs_build_bvh_ex(const gs_gaussians *g, const gs_build_options *opt, gs_bvh **out,
+                          void *stream) {
     if (!out) return fail(GS_ERR_INVALID_ARG, "out is NULL");
+    const int format = opt ? opt->node_format : GS_NODES_BINARY;
+    if (format != GS_NODES_BINARY && format != GS_NODES_WIDE4 && format != GS_NODES_WIDE4_Q8)
+        return fail(GS_ERR_INVALID_ARG, "node_format=%d unknown", format);
+    if (opt)
+        for (int i = 0; i < 7; ++i)
+            if (opt->reserved[i] != 0) return fail(GS_ERR_INVALID_ARG, "reserved options must be zero");
     gs_status st = check_gaussians_host(g, false);
     if (st != GS_OK) return st;
     if ((st = check_device()) != GS_OK) return st;
@@ -122,6 +134,10 @@ gs_status gs_build_bvh(const gs_gaussians *g, gs_bvh **out, void *stream) {
     const int64_t cap = M > 0 ? M : 0;
     const int64_t nn = M > 1 ? M - 1 : 1;
     const int64_t tiles = radix_tiles(cap > 0 ? cap : 1);
+    const int64_t scan_n = 256 * tiles > nn ? 256 * tiles : nn;
+    const bool wide = format != GS_NODES_BINARY;
+    const size_t wide_bytes = format == GS_NODES_WIDE4 ? sizeof(Node4) : sizeof(NodeQ4);
+    b->node_format = format;
     struct Req { void **p; size_t bytes; } reqs[] = {
         {(void **)&b->status, 16},
         {(void **)&b->nodes, (size_t)nn * sizeof(Node)},
@@ -135,9 +151,14 @@ gs_status gs_build_bvh(const gs_gaussians *g, gs_bvh **out, void *stream) {
         {(void **)&b->aabb, (size_t)(cap > 0 ? cap : 1) * 24},
         {(void **)&b->bounds, 64},
         {(void **)&b->hist, (size_t)256 * tiles * 4},
+        {(void **)&b->scan_tmp, (size_t)scan_tmp_entries(scan_n) * 4},
+        {(void **)&b->wide, wide ? (size_t)nn * wide_bytes : 0},
+        {(void **)&b->depth, wide ? (size_t)nn * 4 : 0},
+        {(void **)&b->wmap, wide ? (size_t)nn * 4 : 0},
     };
     int64_t total = 0;
     for (auto &r : reqs) {
+        if (r.bytes == 0) continue;
         cudaError_t e = cudaMalloc(r.p, r.bytes);
         if (e != cudaSuccess) {
             release(b);
@@ -189,6 +210,35 @@ gs_status gs_bvh_get_info(const gs_bvh *b, gs_bvh_info *info) {
     info->device_bytes = b->device_bytes;
     info->node_bytes = (int32_t)sizeof(Node);
     info->prim_bytes = (int32_t)sizeof(PrimRec);
+    info->node_format = b->node_format;
+    info->wide_node_bytes = b->node_format == GS_NODES_WIDE4 ? (int32_t)sizeof(Node4)
+                            : b->node_format == GS_NODES_WIDE4_Q8 ? (int32_t)sizeof(NodeQ4)
+                                                                  : 0;
+    return GS_OK;
+}
+
+gs_status gs_bvh_export_wide(const gs_bvh *b, void *out, int64_t capacity, int64_t *n_out) {
+    if (!b || !n_out) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+    if (b->node_format == GS_NODES_BINARY) return fail(GS_ERR_INVALID_ARG, "handle has binary nodes");
+    if (capacity < 0) return fail(GS_ERR_INVALID_ARG, "negative capacity");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    *n_out = 0;
+    if (b->M == 0) return GS_OK;
+    // count = map of the last internal node + its own flag (even depth)
+    uint32_t last_map = 0, last_depth = 0;
+    const int64_t n_int = b->n_nodes;
+    if ((e = cudaMemcpy(&last_map, b->wmap + n_int - 1, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "copy map");
+    if ((e = cudaMemcpy(&last_depth, b->depth + n_int - 1, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "copy depth");
+    const int64_t n = (int64_t)last_map + ((last_depth & 1u) ? 0 : 1);
+    *n_out = n;
+    const size_t bytes = b->node_format == GS_NODES_WIDE4 ? sizeof(Node4) : sizeof(NodeQ4);
+    const int64_t k = n < capacity ? n : capacity;
+    if (k > 0 && out &&
+        (e = cudaMemcpy(out, b->wide, (size_t)k * bytes, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "copy wide nodes");
     return GS_OK;
 }
 

@@ -21,7 +21,6 @@ namespace {
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kScanThreads = 1024;
 
 // Order-preserving map float -> uint32 (for atomicMin / atomicMax).
 __device__ __forceinline__ unsigned int f2ord(float f) {
@@ -204,37 +203,86 @@ __global__ void __launch_bounds__(kSortThreads)
     hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of len entries by one block of kScanThreads threads.
-__global__ void __launch_bounds__(kScanThreads) k_radix_scan(uint32_t *__restrict__ a, int64_t len) {
-    __shared__ uint32_t warp_sums[kScanThreads / 32];
-    int64_t chunk = (len + kScanThreads - 1) / kScanThreads;
-    int64_t b = threadIdx.x * chunk, e = min(b + chunk, len);
-    uint32_t sum = 0;
-    for (int64_t i = b; i < e; ++i) sum += a[i];
-    // block-wide exclusive scan of the per-thread sums
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t incl = sum;
+// Exclusive scan in three launches: per-block sums, a scan of the block
+// sums by one block, then each block scans its own items and adds its
+// block's offset. kScanItems consecutive entries per block.
+constexpr int kScanItems = 1024;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t warp_sums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
     for (int off = 1; off < 32; off <<= 1) {
-        uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += v;
+        uint32_t u = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += u;
     }
     if (lane == 31) warp_sums[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        uint32_t w = warp_sums[lane];
+        uint32_t w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0u;
         for (int off = 1; off < 32; off <<= 1) {
-            uint32_t v = __shfl_up_sync(0xffffffffu, w, off);
-            if (lane >= off) w += v;
+            uint32_t u = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += u;
         }
         warp_sums[lane] = w;
     }
     __syncthreads();
-    uint32_t run = incl - sum + (warp > 0 ? warp_sums[warp - 1] : 0u);
-    for (int64_t i = b; i < e; ++i) {
-        uint32_t v = a[i];
-        a[i] = run;
-        run += v;
+    const uint32_t excl = incl - v + (warp > 0 ? warp_sums[warp - 1] : 0u);
+    if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return excl;
+}
+
+__global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t *__restrict__ a, int64_t n,
+                                                     uint32_t *__restrict__ sums) {
+    const int64_t base = (int64_t)blockIdx.x * kScanItems;
+    uint32_t v = 0;
+    for (int k = 0; k < kScanItems / 256; ++k) {
+        const int64_t i = base + k * 256 + threadIdx.x;
+        if (i < n) v += a[i];
     }
+    uint32_t total = 0;
+    block_exclusive_scan(v, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(uint32_t *__restrict__ sums, int64_t nb) {
+    const int64_t chunk = (nb + 1023) / 1024;
+    const int64_t b0 = threadIdx.x * chunk, b1 = min(b0 + chunk, nb);
+    uint32_t v = 0;
+    for (int64_t i = b0; i < b1; ++i) v += sums[i];
+    uint32_t run = block_exclusive_scan(v, nullptr);
+    for (int64_t i = b0; i < b1; ++i) {
+        const uint32_t t = sums[i];
+        sums[i] = run;
+        run += t;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_apply(uint32_t *__restrict__ a, int64_t n,
+                                                    const uint32_t *__restrict__ sums) {
+    const int64_t base = (int64_t)blockIdx.x * kScanItems;
+    constexpr int P = kScanItems / 256;  // items per thread, consecutive
+    uint32_t v[P];
+    uint32_t local = 0;
+    for (int k = 0; k < P; ++k) {
+        const int64_t i = base + threadIdx.x * P + k;
+        v[k] = i < n ? a[i] : 0u;
+        local += v[k];
+    }
+    uint32_t run = block_exclusive_scan(local, nullptr) + sums[blockIdx.x];
+    for (int k = 0; k < P; ++k) {
+        const int64_t i = base + threadIdx.x * P + k;
+        if (i < n) a[i] = run;
+        run += v[k];
+    }
+}
+
+void scan_exclusive(uint32_t *a, int64_t n, uint32_t *sums, cudaStream_t s) {
+    const int64_t nb = (n + kScanItems - 1) / kScanItems;
+    k_scan_reduce<<<(unsigned)nb, 256, 0, s>>>(a, n, sums);
+    k_scan_top<<<1, 1024, 0, s>>>(sums, nb);
+    k_scan_apply<<<(unsigned)nb, 256, 0, s>>>(a, n, sums);
 }
 
 // Stable scatter: keys of a tile are ranked in input order, round by round
@@ -397,6 +445,110 @@ __global__ void k_single(const uint32_t *__restrict__ order, const float *__rest
     nodes[0] = nd;
 }
 
+// Depth of every internal binary node (walk to the root).
+__global__ void k_depth(int64_t n_int, const uint32_t *__restrict__ parent_int,
+                        uint32_t *__restrict__ depth, uint32_t *__restrict__ flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    uint32_t d = 0, p = (uint32_t)i;
+    while (p != 0 && d < 4096) {
+        p = parent_int[p];
+        ++d;
+    }
+    depth[i] = d;
+    flag[i] = (d & 1u) ? 0u : 1u;  // wide nodes sit at even binary depth
+}
+
+// Quantisation of one axis of a node: planes origin + q * 2^e, q in 0..255.
+__device__ __forceinline__ int quant_exponent(float ext) {
+    if (!(ext > 0.0f)) return -120;
+    int e = (int)ceilf(log2f(ext / 254.0f));
+    e = max(e, -120);
+    while (254.0f * ldexpf(1.0f, e) < ext) ++e;  // one unit of slack
+    return min(e, 120);
+}
+
+__device__ __forceinline__ unsigned char quant_lo(float v, float origin, float scale) {
+    if (!(v == v)) return 0;  // NaN box: full range
+    float q = floorf((v - origin) / scale);
+    q = fminf(fmaxf(q, 0.0f), 255.0f);
+    while (q > 0.0f && __fadd_rn(origin, q * scale) > v) q -= 1.0f;
+    return (unsigned char)q;
+}
+
+__device__ __forceinline__ unsigned char quant_hi(float v, float origin, float scale) {
+    if (!(v == v)) return 255;
+    float q = ceilf((v - origin) / scale);
+    q = fminf(fmaxf(q, 0.0f), 255.0f);
+    while (q < 255.0f && __fadd_rn(origin, q * scale) < v) q += 1.0f;
+    return (unsigned char)q;
+}
+
+// One wide node per even-depth binary node: its children, or grandchildren
+// where a child is internal; written at its compact index.
+template <int FMT>
+__global__ void k_collapse(int64_t n_int, const Node *__restrict__ nodes,
+                           const uint32_t *__restrict__ depth, const uint32_t *__restrict__ wmap,
+                           void *__restrict__ wide) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int || (depth[i] & 1u)) return;
+    float lo[3][4], hi[3][4];
+    uint32_t child[4];
+    int k = 0;
+    const Node nd = nodes[i];
+    for (int side = 0; side < 2; ++side) {
+        const uint32_t c = nd.child[side];
+        if (c & kLeafBit) {
+            for (int a = 0; a < 3; ++a) { lo[a][k] = nd.box[side][a]; hi[a][k] = nd.box[side][3 + a]; }
+            child[k++] = c;
+        } else {
+            const Node cn = nodes[c];
+            for (int s2 = 0; s2 < 2; ++s2) {
+                for (int a = 0; a < 3; ++a) { lo[a][k] = cn.box[s2][a]; hi[a][k] = cn.box[s2][3 + a]; }
+                const uint32_t gc = cn.child[s2];
+                child[k++] = (gc & kLeafBit) ? gc : wmap[gc];
+            }
+        }
+    }
+    const int used = k;
+    for (; k < 4; ++k) {
+        for (int a = 0; a < 3; ++a) { lo[a][k] = INFINITY; hi[a][k] = INFINITY; }
+        child[k] = kEmpty;
+    }
+    const uint32_t w = wmap[i];
+    if (FMT == GS_NODES_WIDE4) {
+        Node4 n;
+        for (int a = 0; a < 3; ++a)
+            for (int j = 0; j < 4; ++j) { n.lo[a][j] = lo[a][j]; n.hi[a][j] = hi[a][j]; }
+        for (int j = 0; j < 4; ++j) { n.child[j] = child[j]; n.reserved[j] = 0; }
+        reinterpret_cast<Node4 *>(wide)[w] = n;
+    } else {
+        NodeQ4 n;
+        n.used = (unsigned char)((1u << used) - 1u);
+        for (int a = 0; a < 3; ++a) {
+            float nlo = INFINITY, nhi = -INFINITY;
+            for (int j = 0; j < used; ++j) { nlo = fminf(nlo, lo[a][j]); nhi = fmaxf(nhi, hi[a][j]); }
+            if (!(nlo <= nhi)) { nlo = 0.0f; nhi = 0.0f; }
+            const int e = quant_exponent(nhi - nlo);
+            const float scale = ldexpf(1.0f, e);
+            n.origin[a] = nlo;
+            n.exp[a] = (signed char)e;
+            for (int j = 0; j < 4; ++j) {
+                if (j < used) {
+                    n.qlo[a][j] = quant_lo(lo[a][j], nlo, scale);
+                    n.qhi[a][j] = quant_hi(hi[a][j], nlo, scale);
+                } else {
+                    n.qlo[a][j] = 255;
+                    n.qhi[a][j] = 0;
+                }
+            }
+        }
+        for (int j = 0; j < 4; ++j) n.child[j] = child[j];
+        n.reserved[0] = n.reserved[1] = 0;
+        reinterpret_cast<NodeQ4 *>(wide)[w] = n;
+    }
+}
+
 inline unsigned grid_for(int64_t n, int threads) {
     return (unsigned)((n + threads - 1) / threads);
 }
@@ -404,6 +556,8 @@ inline unsigned grid_for(int64_t n, int threads) {
 }  // namespace
 
 int64_t radix_tiles(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+
+int64_t scan_tmp_entries(int64_t n) { return (n + kScanItems - 1) / kScanItems + 1; }
 
 gs_status build_into(gs_bvh *b, const gs_gaussians *g, cudaStream_t s) {
     const int64_t M = g->M;
@@ -424,7 +578,7 @@ gs_status build_into(gs_bvh *b, const gs_gaussians *g, cudaStream_t s) {
     int cur = 0;
     for (int shift = 0; shift < 64; shift += 8) {
         k_radix_hist<<<(unsigned)tiles, kSortThreads, 0, s>>>(M, b->codes[cur], shift, b->hist, tiles);
-        k_radix_scan<<<1, kScanThreads, 0, s>>>(b->hist, 256 * tiles);
+        scan_exclusive(b->hist, 256 * tiles, b->scan_tmp, s);
         k_radix_scatter<<<(unsigned)tiles, kSortThreads, 0, s>>>(
             M, b->codes[cur], b->vals[cur], b->codes[1 - cur], b->vals[1 - cur], shift, b->hist,
             tiles);
@@ -444,6 +598,22 @@ gs_status build_into(gs_bvh *b, const gs_gaussians *g, cudaStream_t s) {
         k_leaves<<<grid_for(M, 256), 256, 0, s>>>(M, order, g->means, g->log_scales, g->quats,
                                                    g->opacity_logits, b->aabb, b->prims, b->nodes,
                                                    parent_int, parent_leaf, b->arrive);
+    }
+    if (b->node_format != GS_NODES_BINARY) {
+        const int64_t n_int = b->n_nodes;
+        if (M == 1) {
+            if ((e = cudaMemsetAsync(b->depth, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "memset depth");
+            if ((e = cudaMemsetAsync(b->wmap, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "memset map");
+        } else {
+            k_depth<<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->parent, b->depth, b->wmap);
+            scan_exclusive(b->wmap, n_int, b->scan_tmp, s);
+        }
+        if (b->node_format == GS_NODES_WIDE4)
+            k_collapse<GS_NODES_WIDE4><<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->nodes, b->depth,
+                                                                            b->wmap, b->wide);
+        else
+            k_collapse<GS_NODES_WIDE4_Q8><<<grid_for(n_int, 256), 256, 0, s>>>(
+                n_int, b->nodes, b->depth, b->wmap, b->wide);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "build launch");
     return GS_OK;

@@ -34,8 +34,33 @@ struct __align__(16) Node {
 };
 static_assert(sizeof(Node) == 64, "Node must be 64 bytes");
 
+// 4-wide node, 128 bytes: child boxes as structure of arrays (FP32).
+struct __align__(16) Node4 {
+    float lo[3][4];  // lo[axis][slot]
+    float hi[3][4];
+    uint32_t child[4];
+    uint32_t reserved[4];
+};
+static_assert(sizeof(Node4) == 128, "Node4 must be 128 bytes");
+
+// 4-wide node, 64 bytes, child boxes quantised to 8 bits per plane against
+// the node's own box: plane = origin[a] + q * 2^exp[a], with the lower
+// planes rounded down and the upper planes rounded up so every decoded box
+// contains the child's FP32 box.
+struct __align__(16) NodeQ4 {
+    float origin[3];
+    signed char exp[3];
+    unsigned char used;   // bit k: slot k holds a child
+    unsigned char qlo[3][4];
+    unsigned char qhi[3][4];
+    uint32_t child[4];
+    uint32_t reserved[2];
+};
+static_assert(sizeof(NodeQ4) == 64, "NodeQ4 must be 64 bytes");
+
 constexpr uint32_t kLeafBit = 0x80000000u;
-constexpr int kMaxStack = 64;
+constexpr uint32_t kEmpty = 0xffffffffu;
+constexpr int kMaxStack = 96;
 constexpr uint32_t kStepLimit = 1u << 22;  // node visits per ray and pass
 
 // Device status word bits.
@@ -70,7 +95,13 @@ struct gs_bvh {
     unsigned int *bounds;  // [6] ordered-int scene bounds of the means
     uint32_t *hist;     // radix histograms [256 * tiles]
     int64_t hist_len;
+    uint32_t *scan_tmp; // block sums of the multi-block scan
     int final_buf;      // which of codes/vals holds the sorted result
+    // traversal nodes other than the binary ones
+    int node_format;    // GS_NODES_*
+    void *wide;         // Node4 or NodeQ4 array, compact
+    uint32_t *depth;    // depth of every internal binary node
+    uint32_t *wmap;     // binary internal node -> wide node index
 };
 
 namespace gsrt {
@@ -83,6 +114,7 @@ bool is_device_ptr(const void *p);
 // Build pipeline (build.cu)
 gs_status build_into(gs_bvh *b, const gs_gaussians *g, cudaStream_t s);
 int64_t radix_tiles(int64_t n);
+int64_t scan_tmp_entries(int64_t n);
 
 // Backward (backward.cu)
 gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,

@@ -2,7 +2,8 @@
 //
 // Same kernels and results as gs_build_bvh, for callers that must not call
 // cudaMalloc: the caller passes the output buffers, and the build scratch
-// (sort keys and ids, parents, arrival counters, boxes, histograms, status)
+// (sort keys and ids, parents, arrival counters, boxes, histograms, scan
+// block sums, status)
 // lives in one file-scope __device__ array sized for at most
 // kNoAllocMaxGaussians Gaussians. Every GPU that loads this library holds
 // that array (about 4 MB) until the process exits.
@@ -31,7 +32,9 @@ constexpr size_t kAabb = kArrive + align_up(4 * kNoAllocMaxGaussians);
 constexpr size_t kBounds = kAabb + align_up(24 * kNoAllocMaxGaussians);
 constexpr size_t kHist = kBounds + align_up(64);
 constexpr size_t kHistEntries = 256 * ((kNoAllocMaxGaussians + 2047) / 2048);
-constexpr size_t kStatus = kHist + align_up(4 * kHistEntries);
+constexpr size_t kScanTmp = kHist + align_up(4 * kHistEntries);
+constexpr size_t kScanTmpEntries = kHistEntries / 1024 + 2;
+constexpr size_t kStatus = kScanTmp + align_up(4 * kScanTmpEntries);
 constexpr size_t kScratchBytes = kStatus + align_up(16);
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -108,6 +111,8 @@ extern "C" gs_status gs_build_bvh_noalloc(const gs_gaussians *g, void *nodes_out
     b.bounds = reinterpret_cast<unsigned int *>(s + kBounds);
     b.hist = reinterpret_cast<uint32_t *>(s + kHist);
     b.hist_len = (int64_t)kHistEntries;
+    b.scan_tmp = reinterpret_cast<uint32_t *>(s + kScanTmp);
+    b.node_format = GS_NODES_BINARY;
     b.status = status_out ? status_out : reinterpret_cast<uint32_t *>(s + kStatus);
     if (!status_out) {
         // the shared status word keeps the last call's contents: clear it

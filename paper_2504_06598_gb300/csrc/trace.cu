@@ -35,7 +35,7 @@ namespace {
 // Persistent kernel: each warp repeatedly takes the next 8x4 pixel tile
 // (one atomic per tile, so the tail of the launch stays balanced), then
 // runs all passes of its 32 pixels.
-template <int N, bool COUNT>
+template <int N, bool COUNT, int FMT>
 __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;
@@ -71,8 +71,12 @@ __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
             for (int k = 0; k < N; ++k) r.slot[k] = Slot{INFINITY, INFINITY, 0.0f, 0xffffffffu};
             update_clip(r, a.t_max);
             if (!valid) r.t_far = -INFINITY;  // lanes off the image never hit
-            if (a.n_nodes > 0)
-                traverse_packet<N, COUNT>(a, r, pass, stack, stack_t, err, cnt);
+            if (a.n_nodes > 0) {
+                if (FMT == GS_NODES_BINARY)
+                    traverse_packet<N, COUNT>(a, r, pass, stack, stack_t, err, cnt);
+                else
+                    traverse_packet_wide<N, COUNT, FMT>(a, r, pass, stack, stack_t, err, cnt);
+            }
             if (valid) {
                 // shade each slot once (Eq. 6) and accumulate (Eq. 7)
                 float Y[16];
@@ -118,14 +122,14 @@ __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
     }
 }
 
-template <int N>
-gs_status launch_n(const TraceArgs &a, bool count, cudaStream_t s) {
+template <int N, int FMT>
+gs_status launch_nf(const TraceArgs &a, bool count, cudaStream_t s) {
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = count ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<N, true>, kThreads, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<N, false>, kThreads, 0);
+        e = count ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<N, true, FMT>, kThreads, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<N, false, FMT>, kThreads, 0);
     if (e != cudaSuccess) return cuda_fail(e, "trace launch setup");
     // one resident grid; warps take tiles until none is left
     const uint32_t tiles = (uint32_t)(((a.width + 7) / 8) * ((a.height + 3) / 4));
@@ -135,9 +139,18 @@ gs_status launch_n(const TraceArgs &a, bool count, cudaStream_t s) {
     if (blocks > max_blocks) blocks = max_blocks;
     if ((e = cudaMemsetAsync(a.work, 0, sizeof(uint32_t), s)) != cudaSuccess)
         return cuda_fail(e, "reset work counter");
-    if (count) k_trace<N, true><<<blocks, kThreads, 0, s>>>(a);
-    else k_trace<N, false><<<blocks, kThreads, 0, s>>>(a);
+    if (count) k_trace<N, true, FMT><<<blocks, kThreads, 0, s>>>(a);
+    else k_trace<N, false, FMT><<<blocks, kThreads, 0, s>>>(a);
     return GS_OK;
+}
+
+template <int N>
+gs_status launch_n(const TraceArgs &a, int format, bool count, cudaStream_t s) {
+    switch (format) {
+        case GS_NODES_WIDE4: return launch_nf<N, GS_NODES_WIDE4>(a, count, s);
+        case GS_NODES_WIDE4_Q8: return launch_nf<N, GS_NODES_WIDE4_Q8>(a, count, s);
+        default: return launch_nf<N, GS_NODES_BINARY>(a, count, s);
+    }
 }
 
 }  // namespace
@@ -147,6 +160,7 @@ gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole 
                        cudaStream_t s) {
     TraceArgs a;
     a.nodes = b->nodes;
+    a.wide = b->wide;
     a.prims = b->prims;
     a.sh = g->sh;
     a.n_nodes = b->n_nodes;
@@ -180,10 +194,10 @@ gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole 
     const bool count = p->counters != nullptr;
     gs_status st;
     switch (p->n_hits) {
-        case 1: st = launch_n<1>(a, count, s); break;
-        case 2: st = launch_n<2>(a, count, s); break;
-        case 4: st = launch_n<4>(a, count, s); break;
-        case 8: st = launch_n<8>(a, count, s); break;
+        case 1: st = launch_n<1>(a, b->node_format, count, s); break;
+        case 2: st = launch_n<2>(a, b->node_format, count, s); break;
+        case 4: st = launch_n<4>(a, b->node_format, count, s); break;
+        case 8: st = launch_n<8>(a, b->node_format, count, s); break;
         default: return fail(GS_ERR_INVALID_ARG, "n_hits must be 1, 2, 4 or 8");
     }
     if (st != GS_OK) return st;

@@ -18,6 +18,7 @@ constexpr int kThreads = 128;
 
 struct TraceArgs {
     const Node *nodes;
+    const void *wide;  // Node4 or NodeQ4 when the handle has wide nodes
     const PrimRec *prims;
     const void *sh;
     int64_t n_nodes;
@@ -386,6 +387,173 @@ __device__ __forceinline__ void traverse_packet(const TraceArgs &a, Ray<N> &r, i
         }
         if (mL) { node = cref.x; active = hL; continue; }
         if (mR) { node = cref.y; active = hR; continue; }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            const bool want = stack_t[sp] <= r.t_far;
+            if (__any_sync(kAll, want)) {
+                node = stack[sp];
+                active = want;
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+    }
+}
+
+
+// Child boxes of a wide node as FP32 planes. For the 8-bit form each plane
+// is origin + q * 2^e rounded once, exactly as the build verified it, so a
+// decoded box contains the FP32 box and the (monotone) slab test can only
+// report more hits, never fewer.
+template <int FMT>
+__device__ __forceinline__ void load_wide(const TraceArgs &a, uint32_t node, float box[4][6],
+                                          uint32_t child[4]) {
+    if (FMT == GS_NODES_WIDE4) {
+        const float4 *np = reinterpret_cast<const float4 *>(static_cast<const Node4 *>(a.wide) + node);
+        const float4 lx = __ldg(np), ly = __ldg(np + 1), lz = __ldg(np + 2);
+        const float4 hx = __ldg(np + 3), hy = __ldg(np + 4), hz = __ldg(np + 5);
+        const uint4 c = __ldg(reinterpret_cast<const uint4 *>(np + 6));
+        const float LX[4] = {lx.x, lx.y, lx.z, lx.w}, LY[4] = {ly.x, ly.y, ly.z, ly.w};
+        const float LZ[4] = {lz.x, lz.y, lz.z, lz.w}, HX[4] = {hx.x, hx.y, hx.z, hx.w};
+        const float HY[4] = {hy.x, hy.y, hy.z, hy.w}, HZ[4] = {hz.x, hz.y, hz.z, hz.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            box[k][0] = LX[k]; box[k][1] = LY[k]; box[k][2] = LZ[k];
+            box[k][3] = HX[k]; box[k][4] = HY[k]; box[k][5] = HZ[k];
+        }
+        child[0] = c.x; child[1] = c.y; child[2] = c.z; child[3] = c.w;
+    } else {
+        const uint4 *np = reinterpret_cast<const uint4 *>(static_cast<const NodeQ4 *>(a.wide) + node);
+        const uint4 v0 = __ldg(np), v1 = __ldg(np + 1), v2 = __ldg(np + 2), v3 = __ldg(np + 3);
+        const float origin[3] = {__uint_as_float(v0.x), __uint_as_float(v0.y), __uint_as_float(v0.z)};
+        float scale[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const int e = (int)(signed char)((v0.w >> (8 * ax)) & 0xffu);
+            scale[ax] = __uint_as_float((uint32_t)(e + 127) << 23);
+        }
+        const uint32_t used = (v0.w >> 24) & 0xffu;
+        const uint32_t qlo[3] = {v1.x, v1.y, v1.z};
+        const uint32_t qhi[3] = {v1.w, v2.x, v2.y};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                const float ql = (float)((qlo[ax] >> (8 * k)) & 0xffu);
+                const float qh = (float)((qhi[ax] >> (8 * k)) & 0xffu);
+                box[k][ax] = __fadd_rn(origin[ax], ql * scale[ax]);
+                box[k][3 + ax] = __fadd_rn(origin[ax], qh * scale[ax]);
+            }
+            if (!((used >> k) & 1u)) {
+                box[k][0] = box[k][1] = box[k][2] = INFINITY;
+                box[k][3] = box[k][4] = box[k][5] = INFINITY;
+            }
+        }
+        child[0] = v2.z; child[1] = v2.w; child[2] = v3.x; child[3] = v3.y;
+    }
+}
+
+// Packet traversal of a 4-wide hierarchy. Leaves are tested nearest first
+// per lane; internal children are ordered for the whole warp by their
+// nearest entry over the lanes that reach them, the nearest visited next and
+// the others pushed with each lane's own entry distance.
+template <int N, bool COUNT, int FMT>
+__device__ __forceinline__ void traverse_packet_wide(const TraceArgs &a, Ray<N> &r, int pass,
+                                                     uint32_t *stack, float *stack_t,
+                                                     uint32_t &err, Counts &cnt) {
+    const uint32_t kAll = 0xffffffffu;
+    const bool lane0 = (threadIdx.x & 31) == 0;
+    int sp = 0;
+    uint32_t node = 0, steps = 0;
+    bool active = r.t_far >= a.t_min;
+    for (;;) {
+        if (++steps > a.step_limit) {
+            err |= kErrSteps;
+            break;
+        }
+        if (COUNT) {
+            cnt.nodes += active;
+            cnt.node_fetch += lane0;
+        }
+        float box[4][6];
+        uint32_t C[4];
+        load_wide<FMT>(a, node, box, C);
+        float t[4];
+        bool h[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) h[k] = slab(box[k], r.inv, r.oinv, a.t_min, r.t_far, t[k]);
+        unsigned todo = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (C[k] != kEmpty && (C[k] & kLeafBit) && h[k]) todo |= 1u << k;
+        if (COUNT) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const unsigned w = __ballot_sync(kAll, (todo >> k) & 1u);
+                if (lane0 && w) ++cnt.prim_fetch;
+            }
+        }
+        while (todo) {
+            int best = 0;
+            float bt = INFINITY;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (((todo >> k) & 1u) && !(t[k] >= bt)) { best = k; bt = t[k]; }
+            todo &= ~(1u << best);
+            uint32_t leaf = C[0];
+#pragma unroll
+            for (int k = 1; k < 4; ++k) if (k == best) leaf = C[k];
+            if (COUNT) ++cnt.prims;
+            intersect<N, COUNT>(a, r, leaf & ~kLeafBit, pass, cnt.draws);
+        }
+        uint32_t key[4];
+        int slot[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool in = C[k] != kEmpty && !(C[k] & kLeafBit);
+            h[k] = in && h[k] && t[k] <= r.t_far;
+            key[k] = __reduce_min_sync(kAll, h[k] ? __float_as_uint(fmaxf(t[k], 0.0f)) : 0xffffffffu);
+            slot[k] = k;
+        }
+        // sort four (key, slot) pairs ascending; keys are uniform over the warp
+#define GS_CSWAP(i, j)                                                   \
+    if (key[j] < key[i]) {                                               \
+        const uint32_t tk = key[i]; key[i] = key[j]; key[j] = tk;        \
+        const int ts = slot[i]; slot[i] = slot[j]; slot[j] = ts;         \
+    }
+        GS_CSWAP(0, 1) GS_CSWAP(2, 3) GS_CSWAP(0, 2) GS_CSWAP(1, 3) GS_CSWAP(1, 2)
+#undef GS_CSWAP
+        if (key[0] != 0xffffffffu) {
+            bool overflow = false;
+#pragma unroll
+            for (int j = 3; j >= 1; --j) {
+                if (key[j] == 0xffffffffu) continue;
+                if (sp >= a.stack_depth) { overflow = true; break; }
+                uint32_t c = C[0];
+                float tt = t[0];
+                bool hh = h[0];
+#pragma unroll
+                for (int k = 1; k < 4; ++k)
+                    if (k == slot[j]) { c = C[k]; tt = t[k]; hh = h[k]; }
+                stack[sp] = c;
+                stack_t[sp] = hh ? tt : INFINITY;
+                ++sp;
+            }
+            if (overflow) {
+                err |= kErrStack;
+                break;
+            }
+            uint32_t c = C[0];
+            bool hh = h[0];
+#pragma unroll
+            for (int k = 1; k < 4; ++k)
+                if (k == slot[0]) { c = C[k]; hh = h[k]; }
+            node = c;
+            active = hh;
+            continue;
+        }
         bool found = false;
         while (sp > 0) {
             --sp;
