@@ -285,6 +285,99 @@ gs_status gs_trace_backward(const gs_bvh *bvh, const gs_gaussians *g, const gs_p
 gs_status gs_build_bvh_noalloc(const gs_gaussians *g, void *nodes_out, void *prims_out,
                                uint32_t *status_out, void *stream);
 
+/* ---------------------------------------------------------------------
+ * Batched wavefront rendering: many views, shadows and one bounce.
+ *
+ * The Gaussians are emissive (their SH colour is their radiance, as the
+ * paper assumes for Gaussians mixed with other assets, Sec. 5-6), placed
+ * above an optional Lambertian ground quad (plane y = ground_y, normal +y,
+ * |x|, |z| <= ground_half_extent) lit by point lights. Per sample of pixel
+ * (x, y) of view v (ray id cams[v].ray_id_offset + y * width + x, sample s):
+ *   camera ray (Philox stream tag 0): closest accepted Gaussian (t_g) or the
+ *     ground (t_q); the nearer one shades the sample, the background if none;
+ *   ground point p (float32: t_q = (ground_y - o.y) / d.y, p = o + t_q d with
+ *     p.y = ground_y): radiance = albedo / pi * sum_l I_l V_l cos_l / r_l^2
+ *     + albedo * L_b, where
+ *   V_l (shadow ray to light l, stream tag 1 + l): 1 if no Gaussian is
+ *     accepted on the open segment, i.e. Gaussians cast stochastic soft
+ *     shadows; cos_l = max(0, omega_l.y), omega_l = normalise(light_l - p);
+ *   L_b (bounce ray, stream tag 9, only if bounce != 0): colour of the
+ *     closest accepted Gaussian along d_b, else the background; d_b =
+ *     normalise((0,1,0) + u) with u uniform on the unit sphere, drawn by
+ *     rejection from Philox-4x32-10 lanes (key = seed, counter = (ray id,
+ *     attempt, s, 16), coordinate 2 * (w >> 8) * 2^-24 - 1, accepted when
+ *     1e-8 < |v|^2 <= 1, up to 16 attempts, else u = (0,1,0)), a
+ *     cosine-weighted direction.
+ * Secondary rays start at p with t_min = shadow_eps; every vector above is
+ * float32, each operation rounded once (normalise as for camera rays).
+ * --------------------------------------------------------------------- */
+typedef struct gs_light {
+    float position[3];
+    float intensity[3];
+} gs_light;
+
+typedef struct gs_scene_extras {
+    int32_t n_lights;           /* 0..8 */
+    gs_light lights[8];
+    int32_t has_ground;         /* 0 or 1 */
+    float ground_y;
+    float ground_half_extent;
+    float ground_albedo[3];
+    int32_t bounce;             /* 0 or 1 */
+    float shadow_eps;           /* t_min of shadow and bounce rays, > 0 */
+} gs_scene_extras;
+
+/* Launch shape of the wavefront kernel (picked by an autotuner).
+ *   block_threads  threads per block: 64, 128 or 256 (0 = 128)
+ *   stack_entries  traversal stack capacity: 48 or 96 (0 = 96) */
+typedef struct gs_launch_options {
+    int32_t block_threads;
+    int32_t stack_entries;
+    int32_t reserved[6];
+} gs_launch_options;
+
+/* Render n_views pinhole views (1..32, uneven sizes allowed) in one
+ * persistent launch: warps take 8x4 tiles from a queue over all views and
+ * trace each tile's camera, shadow and bounce rays as warp packets.
+ *   bvh, g      as for gs_trace_stochastic (any node format)
+ *   cams        host array [n_views]; ray ids must not overlap
+ *   ex          host struct (above); NULL = no ground, lights or bounce
+ *   p           spp >= 1 passes, n_hits must be 1; bg is the background
+ *   opt         host struct or NULL for defaults
+ *   rgb_out     device float[sum_v width_v * height_v][3], view v starting
+ *               at pixel sum_{u<v} width_u * height_u
+ *   counters    optional device uint64[4] incremented by the launch:
+ *               {camera rays, shadow rays, bounce rays, node fetches by
+ *               warps}
+ *   samples_out optional device int32[spp][total pixels][3], per sample:
+ *               camera hit (Gaussian id, -2 ground, -1 nothing), bounce hit
+ *               (Gaussian id or -1), bit l set when light l was visible
+ * Shares the handle's tile counter with gs_trace_stochastic. */
+gs_status gs_render_views(const gs_bvh *bvh, const gs_gaussians *g, const gs_pinhole *cams,
+                          int32_t n_views, const gs_scene_extras *ex, const gs_trace_params *p,
+                          const gs_launch_options *opt, float *rgb_out,
+                          unsigned long long *counters, int32_t *samples_out, void *stream);
+
+/* A captured frame of the batched form: optionally the hierarchy rebuild
+ * (parameters re-read from the same device arrays at every replay), then
+ * the gs_render_views launch, recorded once as a CUDA graph and replayed
+ * with gs_graph_launch. Arguments as for gs_render_views; `stream` must be
+ * a non-default stream (the legacy default stream cannot be captured).
+ * Every replay renders the same rays with the same keys. */
+typedef struct gs_graph gs_graph;
+
+gs_status gs_graph_capture_views(gs_bvh *bvh, const gs_gaussians *g, int32_t rebuild,
+                                 const gs_pinhole *cams, int32_t n_views,
+                                 const gs_scene_extras *ex, const gs_trace_params *p,
+                                 const gs_launch_options *opt, float *rgb_out, void *stream,
+                                 gs_graph **out);
+
+/* Replay a captured frame on `stream` (asynchronous). */
+gs_status gs_graph_launch(gs_graph *graph, void *stream);
+
+/* Release a captured frame. NULL is accepted. */
+gs_status gs_graph_free(gs_graph *graph);
+
 /* Short description of a status code (static string). */
 const char *gs_status_string(gs_status s);
 

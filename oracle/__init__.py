@@ -92,6 +92,9 @@ def _load():
             lib.orc_grad_pinhole.restype = C.c_int
             lib.orc_grad_pinhole.argtypes = [P, P, P, C.c_int64, P, P, C.c_int, P, P, P, P, P,
                                              C.c_int]
+            lib.orc_bounce_dir.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, P]
+            lib.orc_render_scene.restype = C.c_int
+            lib.orc_render_scene.argtypes = [P, P, C.c_int32, P, P, C.c_int64, P, P, P, P, C.c_int]
             lib.orc_render_rays.restype = C.c_int
             lib.orc_render_rays.argtypes = [P, P, C.c_int64, P, P, P, P, P, P, P, P, P, C.c_int]
             _lib = lib
@@ -340,3 +343,57 @@ def grad_pinhole(cloud, cam, settings, d_rgb, pixels=None, mode="blend", n_threa
                          _ptr(out["quats"]), _ptr(out["opacity_logits"]), _ptr(out["sh"]),
                          int(n_threads))
     return out
+
+
+# ---------------------------------------------------------------- scenes
+
+class _Light(C.Structure):
+    _fields_ = [("position", C.c_float * 3), ("intensity", C.c_float * 3)]
+
+
+class _Extras(C.Structure):
+    _fields_ = [("n_lights", C.c_int32), ("lights", _Light * 8), ("has_ground", C.c_int32),
+                ("ground_y", C.c_float), ("ground_half_extent", C.c_float),
+                ("ground_albedo", C.c_float * 3), ("bounce", C.c_int32),
+                ("shadow_eps", C.c_float)]
+
+
+def _extras(ex):
+    e = _Extras()
+    e.n_lights = len(ex.lights)
+    for i, (pos, inten) in enumerate(ex.lights):
+        e.lights[i].position[:] = [float(v) for v in pos]
+        e.lights[i].intensity[:] = [float(v) for v in inten]
+    e.has_ground = int(ex.has_ground)
+    e.ground_y = float(ex.ground_y)
+    e.ground_half_extent = float(ex.ground_half_extent)
+    e.ground_albedo[:] = [float(v) for v in ex.ground_albedo]
+    e.bounce = int(ex.bounce)
+    e.shadow_eps = float(ex.shadow_eps)
+    return e
+
+
+def render_scene(cloud, cams, extras, settings, items, want_diag=True, n_threads=0):
+    """Ground, lights and bounce (see gs_oracle.c). items: list of
+    (view index, linear pixel). Returns est [n,3] and diag [n,spp,3]."""
+    lib = _load()
+    h = _SceneHandle(cloud)
+    arr = (_Pinhole * len(cams))(*[_pinhole(c) for c in cams])
+    items = np.asarray(items, np.int64).reshape(-1, 2)
+    v = _c(items[:, 0], np.int32)
+    px = _c(items[:, 1], np.int64)
+    n = len(items)
+    est = np.zeros((n, 3))
+    diag = np.zeros((n, int(settings.spp), 3), np.int32) if want_diag else None
+    ex = _extras(extras)
+    ps = _params(settings)
+    lib.orc_render_scene(h.ref, arr, len(cams), C.byref(ex), C.byref(ps), n, _ptr(v), _ptr(px),
+                         _ptr(est), _ptr(diag), int(n_threads))
+    return {"est": est, "diag": diag}
+
+
+def bounce_dir(seed, ray_id, sample):
+    lib = _load()
+    d = np.zeros(3, np.float32)
+    lib.orc_bounce_dir(int(seed), int(ray_id), int(sample), _ptr(d))
+    return d

@@ -859,3 +859,204 @@ int orc_grad_pinhole(const orc_scene *sc, const orc_pinhole *cam, const orc_para
     free(act);
     return used;
 }
+
+/* ------------------------------------------------------------------ */
+/* Scenes with a ground quad, point lights and one diffuse bounce (the  */
+/* Monte Carlo path-tracing integration of Sec. 5). Gaussians are        */
+/* emissive; the ground is Lambertian. Per sample s of a pixel:          */
+/*   camera ray -> closest accepted Gaussian (t_g) or ground (t_q),       */
+/*   the nearer one shades (ground on ties);                              */
+/*   ground: albedo/pi sum_l I_l V_l cos_l / r_l^2 + albedo L_b,          */
+/*   V_l = no accepted Gaussian on the shadow segment (tag 1 + l),        */
+/*   L_b = colour of the closest accepted Gaussian along a cosine-        */
+/*   weighted bounce direction (tag 9), else the background.              */
+/* Secondary rays are float32 values from fixed sequences of correctly    */
+/* rounded float operations; Gaussian evaluations are FP64.              */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    float position[3];
+    float intensity[3];
+} orc_light;
+
+typedef struct {
+    int32_t n_lights;
+    orc_light lights[8];
+    int32_t has_ground;
+    float ground_y;
+    float ground_half_extent;
+    float ground_albedo[3];
+    int32_t bounce;
+    float shadow_eps;
+} orc_extras;
+
+/* Closest (or, with any_hit, some) accepted Gaussian on a float32 ray with
+ * range (t_min, t_max); returns its id or -1, *t_out its depth. */
+static int64_t accepted_on_ray(const orc_scene *sc, const orc_gauss *act, const float of[3],
+                               const float df[3], double t_min, double t_max, uint64_t seed,
+                               uint32_t ray_id, uint32_t s, uint32_t tag, int any_hit,
+                               double *t_out)
+{
+    double o[3] = {of[0], of[1], of[2]}, d[3] = {df[0], df[1], df[2]};
+    int64_t win = -1;
+    double tw = INFINITY;
+    for (int64_t g = 0; g < sc->M; ++g) {
+        double t, q;
+        gauss1d(&act[g], o, d, &t, &q);
+        if (!(t > t_min && t < t_max)) continue;
+        if (!(q <= ORC_S2)) continue;
+        double alpha = act[g].opacity * exp(-0.5 * q);
+        if (!(orc_xi(seed, ray_id, (uint32_t)g, s, tag) < alpha)) continue;
+        if (win < 0 || lex_less(t, (int32_t)g, tw, (int32_t)win)) {
+            win = g;
+            tw = t;
+            if (any_hit) break;
+        }
+    }
+    if (t_out) *t_out = tw;
+    return win;
+}
+
+static void colour_of(const orc_scene *sc, int64_t g, const float df[3], double rgb[3])
+{
+    double d[3] = {df[0], df[1], df[2]};
+    double Y[16];
+    orc_sh_basis(sc->sh_degree, d, Y);
+    sh_colour(sc, g, Y, rgb);
+}
+
+/* Cosine-weighted bounce direction about +y from Philox draws (exported
+ * for tests). */
+void orc_bounce_dir(uint64_t seed, uint32_t ray_id, uint32_t s, float d[3])
+{
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    float u[3] = {0.0f, 1.0f, 0.0f};
+    for (uint32_t attempt = 0; attempt < 16; ++attempt) {
+        uint32_t ctr[4] = {ray_id, attempt, s, 16u}, w[4];
+        orc_philox4x32_10(ctr, key, w);
+        float v[3];
+        for (int i = 0; i < 3; ++i) {
+            float f = (float)(w[i] >> 8) * (1.0f / 16777216.0f);
+            v[i] = 2.0f * f - 1.0f;
+        }
+        float r2 = v[0] * v[0];
+        r2 = r2 + v[1] * v[1];
+        r2 = r2 + v[2] * v[2];
+        if (r2 > 1e-8f && r2 <= 1.0f) {
+            float n = sqrtf(r2);
+            for (int i = 0; i < 3; ++i) u[i] = v[i] / n;
+            break;
+        }
+    }
+    float b[3] = {u[0], 1.0f + u[1], u[2]};
+    float n2 = b[0] * b[0];
+    n2 = n2 + b[1] * b[1];
+    n2 = n2 + b[2] * b[2];
+    if (!(n2 > 1e-12f)) {
+        d[0] = 0.0f; d[1] = 1.0f; d[2] = 0.0f;
+        return;
+    }
+    float n = sqrtf(n2);
+    for (int i = 0; i < 3; ++i) d[i] = b[i] / n;
+}
+
+/* Exported: render items (view[i], pix[i]) of the given cameras.
+ * est [n][3]; diag [n][spp][3] = {camera hit (id, -2 ground, -1 none),
+ * bounce hit (id or -1), visible-light bits} (nullable). */
+int orc_render_scene(const orc_scene *sc, const orc_pinhole *cams, int32_t n_views,
+                     const orc_extras *ex, const orc_params *p, int64_t n_items,
+                     const int32_t *view, const int64_t *pix, double *est, int32_t *diag,
+                     int n_threads)
+{
+    (void)n_views;
+    orc_gauss *act = activate_all(sc);
+    const int32_t S = p->spp;
+    int used = 1;
+#ifdef _OPENMP
+    if (n_threads <= 0) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
+#endif
+    for (int64_t it = 0; it < n_items; ++it) {
+#ifdef _OPENMP
+        if (it == 0) used = omp_get_num_threads();
+#endif
+        const orc_pinhole *cam = &cams[view[it]];
+        int32_t x = (int32_t)(pix[it] % cam->width), y = (int32_t)(pix[it] / cam->width);
+        double od[3], dd[3];
+        uint32_t rid;
+        orc_camera_ray(cam, x, y, od, dd, &rid);
+        float o[3] = {(float)od[0], (float)od[1], (float)od[2]};
+        float d[3] = {(float)dd[0], (float)dd[1], (float)dd[2]};
+        /* ground point in float32 */
+        int ground = 0;
+        float tq = INFINITY, gp[3] = {0.0f, 0.0f, 0.0f};
+        if (ex && ex->has_ground && d[1] != 0.0f) {
+            tq = (ex->ground_y - o[1]) / d[1];
+            float ax = tq * d[0], az = tq * d[2];
+            gp[0] = o[0] + ax;
+            gp[1] = ex->ground_y;
+            gp[2] = o[2] + az;
+            ground = (double)tq > p->t_min && fabsf(gp[0]) <= ex->ground_half_extent &&
+                     fabsf(gp[2]) <= ex->ground_half_extent;
+            if (!ground) tq = INFINITY;
+        }
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int32_t s = 0; s < S; ++s) {
+            double tg;
+            int64_t g = accepted_on_ray(sc, act, o, d, p->t_min, p->t_max, p->seed, rid,
+                                        (uint32_t)s, p->stream_tag, 0, &tg);
+            double c[3] = {p->bg[0], p->bg[1], p->bg[2]};
+            int32_t dcam = -1, dbounce = -1, dvis = 0;
+            int gauss = g >= 0 && tg < (double)tq;
+            int on_ground = ground && !gauss;
+            if (gauss) {
+                colour_of(sc, g, d, c);
+                dcam = (int32_t)g;
+            }
+            if (on_ground) {
+                c[0] = c[1] = c[2] = 0.0;
+                dcam = -2;
+                for (int l = 0; l < ex->n_lights; ++l) {
+                    float w[3], om[3];
+                    for (int i = 0; i < 3; ++i) w[i] = ex->lights[l].position[i] - gp[i];
+                    float dist2 = w[0] * w[0];
+                    dist2 = dist2 + w[1] * w[1];
+                    dist2 = dist2 + w[2] * w[2];
+                    float dist = sqrtf(dist2);
+                    for (int i = 0; i < 3; ++i) om[i] = w[i] / dist;
+                    if (!(om[1] > 0.0f && dist2 > 0.0f)) continue;
+                    int64_t blocker = accepted_on_ray(sc, act, gp, om, ex->shadow_eps, dist, p->seed,
+                                                      rid, (uint32_t)s, 1u + (uint32_t)l, 1, NULL);
+                    if (blocker >= 0) continue;
+                    dvis |= 1 << l;
+                    for (int ch = 0; ch < 3; ++ch)
+                        c[ch] += (double)ex->ground_albedo[ch] / M_PI *
+                                 (double)ex->lights[l].intensity[ch] * (double)om[1] /
+                                 (double)dist2;
+                }
+                if (ex->bounce) {
+                    float db[3];
+                    orc_bounce_dir(p->seed, rid, (uint32_t)s, db);
+                    int64_t gb = accepted_on_ray(sc, act, gp, db, ex->shadow_eps, INFINITY, p->seed,
+                                                 rid, (uint32_t)s, 9u, 0, NULL);
+                    double lb[3] = {p->bg[0], p->bg[1], p->bg[2]};
+                    if (gb >= 0) {
+                        colour_of(sc, gb, db, lb);
+                        dbounce = (int32_t)gb;
+                    }
+                    for (int ch = 0; ch < 3; ++ch) c[ch] += (double)ex->ground_albedo[ch] * lb[ch];
+                }
+            }
+            for (int ch = 0; ch < 3; ++ch) acc[ch] += c[ch];
+            if (diag) {
+                int32_t *dg = diag + ((size_t)it * S + (size_t)s) * 3;
+                dg[0] = dcam;
+                dg[1] = dbounce;
+                dg[2] = dvis;
+            }
+        }
+        if (est)
+            for (int ch = 0; ch < 3; ++ch) est[3 * it + ch] = acc[ch] / (double)S;
+    }
+    free(act);
+    return used;
+}

@@ -92,6 +92,14 @@ _SIGNATURES = {
                                     C.c_void_p, C.c_void_p, C.c_void_p]),
     "gs_build_bvh_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p]),
+    "gs_render_views": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p]),
+    "gs_graph_capture_views": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                         C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "gs_graph_free": (C.c_int, [C.c_void_p]),
     "gs_status_string": (C.c_char_p, [C.c_int]),
     "gs_last_error": (C.c_char_p, []),
 }
@@ -375,6 +383,129 @@ def render_differentiable(means, log_scales, quats, opacity_logits, sh, sh_degre
     uses the same handle."""
     return StochasticRender.apply(means, log_scales, quats, opacity_logits, sh, sh_degree, cam,
                                   options)
+
+
+# ---------------------------------------------------------------- batched form
+
+
+class _Light(C.Structure):
+    _fields_ = [("position", C.c_float * 3), ("intensity", C.c_float * 3)]
+
+
+class _SceneExtras(C.Structure):
+    _fields_ = [("n_lights", C.c_int32), ("lights", _Light * 8), ("has_ground", C.c_int32),
+                ("ground_y", C.c_float), ("ground_half_extent", C.c_float),
+                ("ground_albedo", C.c_float * 3), ("bounce", C.c_int32),
+                ("shadow_eps", C.c_float)]
+
+
+class _LaunchOptions(C.Structure):
+    _fields_ = [("block_threads", C.c_int32), ("stack_entries", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
+
+
+def _extras_struct(ex):
+    e = _SceneExtras()
+    if ex is None:
+        return e
+    e.n_lights = len(ex.lights)
+    for i, (pos, inten) in enumerate(ex.lights):
+        e.lights[i].position[:] = [float(v) for v in pos]
+        e.lights[i].intensity[:] = [float(v) for v in inten]
+    e.has_ground = int(ex.has_ground)
+    e.ground_y = float(ex.ground_y)
+    e.ground_half_extent = float(ex.ground_half_extent)
+    e.ground_albedo[:] = [float(v) for v in ex.ground_albedo]
+    e.bounce = int(ex.bounce)
+    e.shadow_eps = float(ex.shadow_eps)
+    return e
+
+
+def _views_args(cams, extras, block_threads, stack_entries, seed, spp, t_min, t_max, bg,
+                stack_depth, stream_tag):
+    cams = [c if isinstance(c, Camera) else Camera.of(c) for c in cams]
+    arr = (_Pinhole * len(cams))(*[c.struct() for c in cams])
+    ex = _extras_struct(extras)
+    opt = _LaunchOptions()
+    opt.block_threads = int(block_threads)
+    opt.stack_entries = int(stack_entries)
+    ps = _params(seed, spp, 1, t_min, t_max, bg, stack_depth, stream_tag, None)
+    total = sum(c.width * c.height for c in cams)
+    return cams, arr, ex, opt, ps, total
+
+
+def render_views(bvh: Bvh, g: Gaussians, cams, extras=None, seed=0, spp=1, t_min=0.0,
+                 t_max=float("inf"), bg=(0.0, 0.0, 0.0), stack_depth=0, stream_tag=0,
+                 block_threads=0, stack_entries=0, counters=None, want_samples=False, out=None,
+                 stream=None):
+    """``gs_render_views``: all views in one persistent launch.
+
+    Returns the packed image [total pixels, 3] (view v starts after the
+    pixels of views < v), and the per-sample diagnostics [spp, total, 3]
+    when ``want_samples``."""
+    cams, arr, ex, opt, ps, total = _views_args(cams, extras, block_threads, stack_entries, seed,
+                                                 spp, t_min, t_max, bg, stack_depth, stream_tag)
+    dev = g.means.device
+    rgb = out if out is not None else torch.empty((total, 3), dtype=torch.float32, device=dev)
+    samples = torch.empty((spp, total, 3), dtype=torch.int32, device=dev) if want_samples else None
+    gs_ = g.struct()
+    _check(lib().gs_render_views(
+        bvh.handle, C.byref(gs_), arr, len(cams), C.byref(ex), C.byref(ps), C.byref(opt),
+        C.c_void_p(rgb.data_ptr()), None if counters is None else C.c_void_p(counters.data_ptr()),
+        None if samples is None else C.c_void_p(samples.data_ptr()), _stream_handle(stream)))
+    return (rgb, samples) if want_samples else rgb
+
+
+def split_views(packed, cams):
+    """Packed [total, 3] image -> list of [H, W, 3] views."""
+    out, o = [], 0
+    for c in cams:
+        n = c.width * c.height
+        out.append(packed[o:o + n].reshape(c.height, c.width, 3))
+        o += n
+    return out
+
+
+class FrameGraph:
+    """``gs_graph_capture_views``: one frame (optional rebuild + the batched
+    render) captured as a CUDA graph on a side stream; ``replay()`` runs it."""
+
+    def __init__(self, bvh: Bvh, g: Gaussians, cams, extras=None, rebuild=True, out=None,
+                 stream=None, **kw):
+        self.stream = stream or torch.cuda.Stream()
+        opts = dict(seed=0, spp=1, t_min=0.0, t_max=float("inf"), bg=(0.0, 0.0, 0.0),
+                    stack_depth=0, stream_tag=0, block_threads=0, stack_entries=0)
+        opts.update(kw)
+        cams, arr, ex, opt, ps, total = _views_args(cams, extras, **{
+            k: opts[k] for k in ("block_threads", "stack_entries", "seed", "spp", "t_min",
+                                 "t_max", "bg", "stack_depth", "stream_tag")})
+        self.rgb = out if out is not None else torch.empty((total, 3), dtype=torch.float32,
+                                                           device=g.means.device)
+        self._keep = (bvh, g, arr, ex, opt, ps)
+        gs_ = g.struct()
+        self._gs = gs_
+        h = C.c_void_p()
+        torch.cuda.synchronize()
+        _check(lib().gs_graph_capture_views(
+            bvh.handle, C.byref(gs_), int(bool(rebuild)), arr, len(cams), C.byref(ex),
+            C.byref(ps), C.byref(opt), C.c_void_p(self.rgb.data_ptr()),
+            C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self._h = h
+
+    def replay(self, stream=None):
+        _check(lib().gs_graph_launch(self._h, _stream_handle(stream or self.stream)))
+        return self.rgb
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            lib().gs_graph_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def render(g: Gaussians, cam, stream=None, **kw):

@@ -353,4 +353,134 @@ gs_status gs_trace_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pin
                            d_sh, (cudaStream_t)stream);
 }
 
+static gs_status check_camera(const gs_pinhole *cam) {
+    if (cam->width < 1 || cam->height < 1 || cam->width > 65536 || cam->height > 65536)
+        return fail(GS_ERR_INVALID_ARG, "image size %dx%d out of range", cam->width, cam->height);
+    if ((uint64_t)cam->ray_id_offset + (uint64_t)cam->width * (uint64_t)cam->height >
+        0x100000000ull)
+        return fail(GS_ERR_INVALID_ARG, "ray ids exceed 32 bits");
+    if (!(cam->fov_y_deg > 0.0f && cam->fov_y_deg < 180.0f))
+        return fail(GS_ERR_INVALID_ARG, "fov_y_deg=%g not in (0, 180)", (double)cam->fov_y_deg);
+    for (int i = 0; i < 3; ++i)
+        if (!isfinite(cam->eye[i]) || !isfinite(cam->look_at[i]) || !isfinite(cam->up[i]))
+            return fail(GS_ERR_INVALID_ARG, "camera vectors must be finite");
+    return GS_OK;
+}
+
+gs_status gs_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cams,
+                          int32_t n_views, const gs_scene_extras *ex, const gs_trace_params *p,
+                          const gs_launch_options *opt, float *rgb_out,
+                          unsigned long long *counters, int32_t *samples_out, void *stream) {
+    if (!cams || n_views < 1 || n_views > 32)
+        return fail(GS_ERR_INVALID_ARG, "need 1..32 views, got %d", n_views);
+    gs_status st = check_trace_args(b, g, &cams[0], p);
+    if (st != GS_OK) return st;
+    if (p->n_hits != 1) return fail(GS_ERR_INVALID_ARG, "the wavefront form takes n_hits = 1");
+    for (int v = 0; v < n_views; ++v)
+        if ((st = check_camera(&cams[v])) != GS_OK) return st;
+    for (int v = 0; v < n_views; ++v)
+        for (int u = v + 1; u < n_views; ++u) {
+            const uint64_t a0 = cams[v].ray_id_offset,
+                           a1 = a0 + (uint64_t)cams[v].width * cams[v].height;
+            const uint64_t b0 = cams[u].ray_id_offset,
+                           b1 = b0 + (uint64_t)cams[u].width * cams[u].height;
+            if (a0 < b1 && b0 < a1)
+                return fail(GS_ERR_INVALID_ARG, "ray ids of views %d and %d overlap", v, u);
+        }
+    if (ex) {
+        if (ex->n_lights < 0 || ex->n_lights > 8) return fail(GS_ERR_INVALID_ARG, "0..8 lights");
+        if ((ex->n_lights > 0 || ex->bounce) && !(ex->shadow_eps > 0.0f && isfinite(ex->shadow_eps)))
+            return fail(GS_ERR_INVALID_ARG, "shadow_eps must be > 0");
+        if (ex->has_ground && !(ex->ground_half_extent >= 0.0f && isfinite(ex->ground_y)))
+            return fail(GS_ERR_INVALID_ARG, "bad ground plane");
+        for (int l = 0; l < ex->n_lights; ++l)
+            for (int i = 0; i < 3; ++i)
+                if (!isfinite(ex->lights[l].position[i]) || !isfinite(ex->lights[l].intensity[i]))
+                    return fail(GS_ERR_INVALID_ARG, "lights must be finite");
+    }
+    if (opt) {
+        if (opt->block_threads != 0 && opt->block_threads != 64 && opt->block_threads != 128 &&
+            opt->block_threads != 256)
+            return fail(GS_ERR_INVALID_ARG, "block_threads must be 64, 128 or 256");
+        if (opt->stack_entries != 0 && opt->stack_entries != 48 && opt->stack_entries != 96)
+            return fail(GS_ERR_INVALID_ARG, "stack_entries must be 48 or 96");
+    }
+    if (!rgb_out) return fail(GS_ERR_INVALID_ARG, "rgb_out is NULL");
+    if ((st = check_device()) != GS_OK) return st;
+    if ((st = check_gaussians_device(g, true)) != GS_OK) return st;
+    if (!is_device_ptr(rgb_out)) return fail(GS_ERR_INVALID_ARG, "rgb_out is not a device pointer");
+    if (counters && !is_device_ptr(counters))
+        return fail(GS_ERR_INVALID_ARG, "counters is not a device pointer");
+    if (samples_out && !is_device_ptr(samples_out))
+        return fail(GS_ERR_INVALID_ARG, "samples_out is not a device pointer");
+    return launch_render_views(b, g, cams, n_views, ex, p, opt, rgb_out, counters, samples_out,
+                               (cudaStream_t)stream);
+}
+
+struct gs_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+gs_status gs_graph_capture_views(gs_bvh *b, const gs_gaussians *g, int32_t rebuild,
+                                 const gs_pinhole *cams, int32_t n_views,
+                                 const gs_scene_extras *ex, const gs_trace_params *p,
+                                 const gs_launch_options *opt, float *rgb_out, void *stream,
+                                 gs_graph **out) {
+    if (!out) return fail(GS_ERR_INVALID_ARG, "out is NULL");
+    if (!stream) return fail(GS_ERR_INVALID_ARG, "capture needs a non-default stream");
+    if (rebuild) {
+        gs_status st = check_gaussians_host(g, false);
+        if (st != GS_OK) return st;
+        if (!b || g->M > b->capacity) return fail(GS_ERR_INVALID_ARG, "rebuild exceeds capacity");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    gs_status st = GS_OK;
+    if (rebuild) {
+        b->M = g->M;
+        st = build_into(b, g, s);
+    }
+    if (st == GS_OK)
+        st = gs_render_views(b, g, cams, n_views, ex, p, opt, rgb_out, nullptr, nullptr, stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(s, &graph);
+    if (st != GS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    cudaGraphExec_t exec = nullptr;
+    if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(e, "instantiate graph");
+    }
+    gs_graph *gr = (gs_graph *)calloc(1, sizeof(gs_graph));
+    if (!gr) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return fail(GS_ERR_OOM, "host allocation failed");
+    }
+    gr->graph = graph;
+    gr->exec = exec;
+    *out = gr;
+    return GS_OK;
+}
+
+gs_status gs_graph_launch(gs_graph *gr, void *stream) {
+    if (!gr) return fail(GS_ERR_INVALID_ARG, "graph is NULL");
+    cudaError_t e = cudaGraphLaunch(gr->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    return GS_OK;
+}
+
+gs_status gs_graph_free(gs_graph *gr) {
+    if (!gr) return GS_OK;
+    cudaGraphExecDestroy(gr->exec);
+    cudaGraphDestroy(gr->graph);
+    free(gr);
+    return GS_OK;
+}
+
 }  // extern "C"

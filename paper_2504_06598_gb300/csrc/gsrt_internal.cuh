@@ -122,6 +122,12 @@ gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinho
                           float *d_log_scales, float *d_quats, float *d_logits, float *d_sh,
                           cudaStream_t s);
 
+// Wavefront (wavefront.cu)
+gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cams,
+                              int n_views, const gs_scene_extras *ex, const gs_trace_params *p,
+                              const gs_launch_options *opt, float *rgb, unsigned long long *counters,
+                              int32_t *samples, cudaStream_t s);
+
 // Trace (trace.cu)
 gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
                        const gs_trace_params *p, float *rgb, int32_t *hit_id, float *hit_t,

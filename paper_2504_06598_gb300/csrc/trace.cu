@@ -57,14 +57,16 @@ __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
         const bool valid = x < a.width && y < a.height;
         const int64_t pix = valid ? (int64_t)y * a.width + x : 0;
         Ray<N> r;
-        camera_ray(a, valid ? x : 0, valid ? y : 0, r.d);
-        for (int i = 0; i < 3; ++i) {
-            r.o[i] = a.eye[i];
-            const float di = fabsf(r.d[i]) < 1e-30f ? copysignf(1e-30f, r.d[i]) : r.d[i];
-            r.inv[i] = 1.0f / di;
-            r.oinv[i] = r.o[i] * r.inv[i];
+        {
+            float d[3];
+            camera_ray(a, valid ? x : 0, valid ? y : 0, d);
+            set_ray(r, a.eye, d);
         }
         r.ray_id = a.ray_id_offset + (uint32_t)pix;
+        r.stream_tag = a.stream_tag;
+        r.t_min = a.t_min;
+        r.t_max = a.t_max;
+        r.any_hit = false;
         float acc[3] = {0.0f, 0.0f, 0.0f};
         for (int pass = 0; pass < a.spp; ++pass) {
 #pragma unroll

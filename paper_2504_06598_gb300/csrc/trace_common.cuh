@@ -90,19 +90,25 @@ __device__ __forceinline__ void cross_rn(const float a[3], const float b[3], flo
     c[2] = __fsub_rn(__fmul_rn(a[0], b[1]), __fmul_rn(a[1], b[0]));
 }
 
-__device__ __forceinline__ void camera_ray(const TraceArgs &a, int x, int y, float d[3]) {
+__device__ __forceinline__ void camera_ray_view(const float eye[3], const float look_at[3],
+                                                const float up[3], float tan_half, int width,
+                                                int height, int x, int y, float d[3]) {
     float f[3], r[3], u[3];
-    for (int i = 0; i < 3; ++i) f[i] = __fsub_rn(a.look_at[i], a.eye[i]);
+    for (int i = 0; i < 3; ++i) f[i] = __fsub_rn(look_at[i], eye[i]);
     normalise_rn(f);
-    cross_rn(f, a.up, r);
+    cross_rn(f, up, r);
     normalise_rn(r);
     cross_rn(r, f, u);
-    const float s = __fdiv_rn(a.tan_half, (float)a.height);
-    const float ux = __fmul_rn((float)(2 * x + 1 - a.width), s);
-    const float uy = __fmul_rn((float)(a.height - 1 - 2 * y), s);
+    const float s = __fdiv_rn(tan_half, (float)height);
+    const float ux = __fmul_rn((float)(2 * x + 1 - width), s);
+    const float uy = __fmul_rn((float)(height - 1 - 2 * y), s);
     for (int i = 0; i < 3; ++i)
         d[i] = __fadd_rn(__fadd_rn(f[i], __fmul_rn(ux, r[i])), __fmul_rn(uy, u[i]));
     normalise_rn(d);
+}
+
+__device__ __forceinline__ void camera_ray(const TraceArgs &a, int x, int y, float d[3]) {
+    camera_ray_view(a.eye, a.look_at, a.up, a.tan_half, a.width, a.height, x, y, d);
 }
 
 // ---------------------------------------------------------------- SH colour
@@ -202,9 +208,30 @@ template <int N>
 struct Ray {
     float o[3], d[3], inv[3], oinv[3];
     uint32_t ray_id;
+    uint32_t stream_tag;  // fourth Philox counter word
+    float t_min, t_max;   // valid range of the 1D mean (Alg. 1)
+    bool any_hit;         // stop at the first accepted hit (shadow rays)
     Slot slot[N];
     float t_far;  // conservative traversal clip
 };
+
+// Origin, unit direction and the slab-test reciprocals of a ray.
+template <int N>
+__device__ __forceinline__ void set_ray(Ray<N> &r, const float o[3], const float d[3]) {
+    for (int i = 0; i < 3; ++i) {
+        r.o[i] = o[i];
+        r.d[i] = d[i];
+        const float di = fabsf(d[i]) < 1e-30f ? copysignf(1e-30f, d[i]) : d[i];
+        r.inv[i] = 1.0f / di;
+        r.oinv[i] = r.o[i] * r.inv[i];
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void reset_slots(Ray<N> &r) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) r.slot[k] = Slot{INFINITY, INFINITY, 0.0f, 0xffffffffu};
+}
 
 template <int N>
 __device__ __forceinline__ void update_clip(Ray<N> &r, float t_max) {
@@ -252,7 +279,7 @@ __device__ __forceinline__ void intersect(const TraceArgs &a, Ray<N> &r, uint32_
     const float tau = -wd * inv_dd;
     const float t = tc + tau;
     // Alg. 1 range test; t_far only prunes hits behind every slot
-    if (!(t > a.t_min) || !(t < a.t_max) || !(t <= r.t_far)) return;
+    if (!(t > r.t_min) || !(t < r.t_max) || !(t <= r.t_far)) return;
     bool closer[N];
     bool any = false;
 #pragma unroll
@@ -276,8 +303,8 @@ __device__ __forceinline__ void intersect(const TraceArgs &a, Ray<N> &r, uint32_
     // Eq. 4: one Philox call serves four consecutive samples
     uint4 u0 = make_uint4(0, 0, 0, 0), u1 = make_uint4(0, 0, 0, 0);
     const uint32_t s0 = (uint32_t)pass * N;
-    u0 = philox10(make_uint4(r.ray_id, gid, s0 >> 2, a.stream_tag), a.key0, a.key1);
-    if (N == 8) u1 = philox10(make_uint4(r.ray_id, gid, (s0 >> 2) + 1, a.stream_tag), a.key0, a.key1);
+    u0 = philox10(make_uint4(r.ray_id, gid, s0 >> 2, r.stream_tag), a.key0, a.key1);
+    if (N == 8) u1 = philox10(make_uint4(r.ray_id, gid, (s0 >> 2) + 1, r.stream_tag), a.key0, a.key1);
     if (COUNT) n_draws += 1 + (N == 8);
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -291,7 +318,8 @@ __device__ __forceinline__ void intersect(const TraceArgs &a, Ray<N> &r, uint32_
             r.slot[k].gid = gid;
         }
     }
-    update_clip(r, a.t_max);
+    update_clip(r, r.t_max);
+    if (r.any_hit && r.slot[0].gid != 0xffffffffu) r.t_far = -INFINITY;  // visibility known
 }
 
 // Slab test of one child box against [t_min, t_far].
@@ -331,7 +359,7 @@ __device__ __forceinline__ void traverse_packet(const TraceArgs &a, Ray<N> &r, i
     const bool lane0 = (threadIdx.x & 31) == 0;
     int sp = 0;
     uint32_t node = 0, steps = 0;
-    bool active = r.t_far >= a.t_min;  // this lane's ray entered the node
+    bool active = r.t_far >= r.t_min;  // this lane's ray entered the node
     for (;;) {
         if (++steps > a.step_limit) {
             err |= kErrSteps;
@@ -347,8 +375,8 @@ __device__ __forceinline__ void traverse_packet(const TraceArgs &a, Ray<N> &r, i
         const float boxL[6] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
         const float boxR[6] = {b1.z, b1.w, b2.x, b2.y, b2.z, b2.w};
         float tL, tR;
-        bool hL = slab(boxL, r.inv, r.oinv, a.t_min, r.t_far, tL);
-        bool hR = slab(boxR, r.inv, r.oinv, a.t_min, r.t_far, tR);
+        bool hL = slab(boxL, r.inv, r.oinv, r.t_min, r.t_far, tL);
+        bool hR = slab(boxR, r.inv, r.oinv, r.t_min, r.t_far, tR);
         const bool leafL = (cref.x & kLeafBit) != 0u, leafR = (cref.y & kLeafBit) != 0u;
         if (leafL || leafR) {
             // Alg. 1 on the leaves this lane's ray reaches, nearer box first
@@ -467,7 +495,7 @@ __device__ __forceinline__ void traverse_packet_wide(const TraceArgs &a, Ray<N> 
     const bool lane0 = (threadIdx.x & 31) == 0;
     int sp = 0;
     uint32_t node = 0, steps = 0;
-    bool active = r.t_far >= a.t_min;
+    bool active = r.t_far >= r.t_min;
     for (;;) {
         if (++steps > a.step_limit) {
             err |= kErrSteps;
@@ -483,7 +511,7 @@ __device__ __forceinline__ void traverse_packet_wide(const TraceArgs &a, Ray<N> 
         float t[4];
         bool h[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) h[k] = slab(box[k], r.inv, r.oinv, a.t_min, r.t_far, t[k]);
+        for (int k = 0; k < 4; ++k) h[k] = slab(box[k], r.inv, r.oinv, r.t_min, r.t_far, t[k]);
         unsigned todo = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k)

@@ -1,0 +1,362 @@
+// wavefront.cu -- many views, shadows and one diffuse bounce in one
+// persistent launch (the path-tracing integration of Sec. 5: Gaussians
+// among other assets cast soft shadows and light their surroundings).
+//
+// Warps take 8x4 pixel tiles from one queue spanning every view (views of
+// uneven size balance through the queue). For each sample a warp traces,
+// as packets: the camera rays of its tile; for the lanes whose camera ray
+// reaches the ground first, one shadow packet per light (any-hit: a lane
+// stops at its first accepted Gaussian) and one bounce packet (closest
+// accepted Gaussian). Each ray type has its own Philox stream tag, so the
+// draws of the different rays of a sample are independent.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "trace_common.cuh"
+
+namespace gsrt {
+namespace {
+
+constexpr int kMaxViews = 32;
+constexpr int kMaxLights = 8;
+constexpr uint32_t kTagShadow = 1, kTagBounce = 9, kTagBounceDir = 16;
+
+struct ViewDesc {
+    float eye[3], look_at[3], up[3];
+    float tan_half;
+    int width, height;
+    uint32_t ray_id_offset;
+    uint32_t tile_begin;  // first tile of this view in the global queue
+    uint32_t tiles_x;
+    int64_t pix_begin;    // first pixel of this view in the packed output
+};
+
+struct WaveArgs {
+    TraceArgs t;
+    ViewDesc views[kMaxViews];
+    int n_views;
+    uint32_t total_tiles;
+    int n_lights;
+    float light_pos[kMaxLights][3];
+    float light_int[kMaxLights][3];
+    int has_ground;
+    float ground_y, ground_half;
+    float albedo[3];
+    float albedo_over_pi[3];
+    int bounce;
+    float eps;
+    unsigned long long *counters;
+    int32_t *samples;  // optional [spp][n_pix][3] diagnostics
+    int64_t n_pix;
+};
+
+// Bounce direction: cosine-weighted about +y, normalise(n + u) with u
+// uniform on the unit sphere by rejection from Philox lanes.
+__device__ __forceinline__ void bounce_dir(const TraceArgs &a, uint32_t ray_id, uint32_t s,
+                                           float d[3]) {
+    float u[3] = {0.0f, 1.0f, 0.0f};
+    for (uint32_t attempt = 0; attempt < 16; ++attempt) {
+        const uint4 w = philox10(make_uint4(ray_id, attempt, s, kTagBounceDir), a.key0, a.key1);
+        const uint32_t ws[3] = {w.x, w.y, w.z};
+        float v[3];
+        for (int i = 0; i < 3; ++i)
+            v[i] = __fsub_rn(__fmul_rn(2.0f, (float)(ws[i] >> 8) * 0x1p-24f), 1.0f);
+        float r2 = __fmul_rn(v[0], v[0]);
+        r2 = __fadd_rn(r2, __fmul_rn(v[1], v[1]));
+        r2 = __fadd_rn(r2, __fmul_rn(v[2], v[2]));
+        if (r2 > 1e-8f && r2 <= 1.0f) {
+            const float n = __fsqrt_rn(r2);
+            for (int i = 0; i < 3; ++i) u[i] = __fdiv_rn(v[i], n);
+            break;
+        }
+    }
+    float b[3] = {u[0], __fadd_rn(1.0f, u[1]), u[2]};
+    float n2 = __fmul_rn(b[0], b[0]);
+    n2 = __fadd_rn(n2, __fmul_rn(b[1], b[1]));
+    n2 = __fadd_rn(n2, __fmul_rn(b[2], b[2]));
+    if (!(n2 > 1e-12f)) {
+        d[0] = 0.0f; d[1] = 1.0f; d[2] = 0.0f;
+        return;
+    }
+    const float n = __fsqrt_rn(n2);
+    for (int i = 0; i < 3; ++i) d[i] = __fdiv_rn(b[i], n);
+}
+
+template <int FMT, bool COUNT>
+__device__ __forceinline__ void trace_packet(const TraceArgs &a, Ray<1> &r, int pass,
+                                             uint32_t *stack, float *stack_t, uint32_t &err,
+                                             Counts &cnt) {
+    if (a.n_nodes == 0) return;
+    if (FMT == GS_NODES_BINARY) traverse_packet<1, COUNT>(a, r, pass, stack, stack_t, err, cnt);
+    else traverse_packet_wide<1, COUNT, FMT>(a, r, pass, stack, stack_t, err, cnt);
+}
+
+template <int FMT, int STACK, bool COUNT>
+__global__ void k_render_views(const WaveArgs w) {
+    const TraceArgs &a = w.t;
+    const int lane = threadIdx.x & 31;
+    const uint32_t kAll = 0xffffffffu;
+    uint32_t stack[STACK];
+    float stack_t[STACK];
+    uint32_t err = 0;
+    Counts cnt;
+    unsigned long long n_cam = 0, n_shadow = 0, n_bounce = 0;
+    for (;;) {
+        uint32_t tile = 0;
+        if (lane == 0) tile = atomicAdd(a.work, 1u);
+        tile = __shfl_sync(kAll, tile, 0);
+        if (tile >= w.total_tiles) break;
+        int v = 0;
+        while (v + 1 < w.n_views && w.views[v + 1].tile_begin <= tile) ++v;
+        const ViewDesc &vw = w.views[v];
+        const uint32_t lt = tile - vw.tile_begin;
+        const int x = (int)((lt % vw.tiles_x) * 8 + (lane & 7));
+        const int y = (int)((lt / vw.tiles_x) * 4 + (lane >> 3));
+        const bool valid = x < vw.width && y < vw.height;
+        const int64_t lpix = valid ? (int64_t)y * vw.width + x : 0;
+        const uint32_t ray_id = vw.ray_id_offset + (uint32_t)lpix;
+        float d0[3];
+        camera_ray_view(vw.eye, vw.look_at, vw.up, vw.tan_half, vw.width, vw.height,
+                        valid ? x : 0, valid ? y : 0, d0);
+        float Y0[16];
+        sh_basis(a.sh_degree, d0, Y0);
+        // ground hit of the camera ray (fixed for the pixel)
+        bool ground = false;
+        float tq = INFINITY, p[3] = {0.0f, 0.0f, 0.0f};
+        if (w.has_ground && valid && d0[1] != 0.0f) {
+            tq = __fdiv_rn(__fsub_rn(w.ground_y, vw.eye[1]), d0[1]);
+            p[0] = __fadd_rn(vw.eye[0], __fmul_rn(tq, d0[0]));
+            p[1] = w.ground_y;
+            p[2] = __fadd_rn(vw.eye[2], __fmul_rn(tq, d0[2]));
+            ground = tq > a.t_min && fabsf(p[0]) <= w.ground_half && fabsf(p[2]) <= w.ground_half;
+            if (!ground) tq = INFINITY;
+        }
+        // shadow directions and distances (fixed for the pixel)
+        float acc[3] = {0.0f, 0.0f, 0.0f};
+        for (int s = 0; s < a.spp; ++s) {
+            // camera ray
+            Ray<1> r;
+            set_ray(r, vw.eye, d0);
+            r.ray_id = ray_id;
+            r.stream_tag = a.stream_tag;
+            r.t_min = a.t_min;
+            r.t_max = a.t_max;
+            r.any_hit = false;
+            reset_slots(r);
+            update_clip(r, r.t_max);
+            if (!valid) r.t_far = -INFINITY;
+            trace_packet<FMT, COUNT>(a, r, s, stack, stack_t, err, cnt);
+            n_cam += valid;
+            const bool gauss = valid && r.slot[0].gid != 0xffffffffu && r.slot[0].t < tq;
+            const bool on_ground = valid && ground && !gauss;
+            float c[3] = {a.bg[0], a.bg[1], a.bg[2]};
+            int32_t diag_cam = -1, diag_bounce = -1, diag_vis = 0;
+            if (gauss) {
+                sh_colour(a, r.slot[0].gid, Y0, c);
+                diag_cam = (int32_t)r.slot[0].gid;
+            }
+            if (on_ground) {
+                c[0] = c[1] = c[2] = 0.0f;
+                diag_cam = -2;
+            }
+            // one shadow packet per light
+            for (int l = 0; l < w.n_lights; ++l) {
+                float wl[3], omega[3];
+                for (int i = 0; i < 3; ++i) wl[i] = __fsub_rn(w.light_pos[l][i], p[i]);
+                float dist2 = __fmul_rn(wl[0], wl[0]);
+                dist2 = __fadd_rn(dist2, __fmul_rn(wl[1], wl[1]));
+                dist2 = __fadd_rn(dist2, __fmul_rn(wl[2], wl[2]));
+                const float dist = __fsqrt_rn(dist2);
+                for (int i = 0; i < 3; ++i) omega[i] = __fdiv_rn(wl[i], dist);
+                const bool need = on_ground && omega[1] > 0.0f && dist2 > 0.0f;
+                if (!__any_sync(kAll, need)) continue;
+                Ray<1> sr;
+                set_ray(sr, p, need ? omega : d0);
+                sr.ray_id = ray_id;
+                sr.stream_tag = kTagShadow + (uint32_t)l;
+                sr.t_min = w.eps;
+                sr.t_max = dist;
+                sr.any_hit = true;
+                reset_slots(sr);
+                update_clip(sr, sr.t_max);
+                if (!need) sr.t_far = -INFINITY;
+                trace_packet<FMT, COUNT>(a, sr, s, stack, stack_t, err, cnt);
+                n_shadow += need;
+                if (need && sr.slot[0].gid == 0xffffffffu) {
+                    diag_vis |= 1 << l;
+                    const float k = __fdiv_rn(omega[1], dist2);
+                    for (int i = 0; i < 3; ++i)
+                        c[i] = fmaf(w.albedo_over_pi[i] * w.light_int[l][i], k, c[i]);
+                }
+            }
+            // one diffuse bounce
+            if (w.bounce) {
+                float db[3] = {0.0f, 1.0f, 0.0f};
+                if (on_ground) bounce_dir(a, ray_id, (uint32_t)s, db);
+                const bool need = on_ground;
+                if (__any_sync(kAll, need)) {
+                    Ray<1> br;
+                    set_ray(br, p, db);
+                    br.ray_id = ray_id;
+                    br.stream_tag = kTagBounce;
+                    br.t_min = w.eps;
+                    br.t_max = INFINITY;
+                    br.any_hit = false;
+                    reset_slots(br);
+                    update_clip(br, br.t_max);
+                    if (!need) br.t_far = -INFINITY;
+                    trace_packet<FMT, COUNT>(a, br, s, stack, stack_t, err, cnt);
+                    n_bounce += need;
+                    if (need) {
+                        float lb[3] = {a.bg[0], a.bg[1], a.bg[2]};
+                        if (br.slot[0].gid != 0xffffffffu) {
+                            float Yb[16];
+                            sh_basis(a.sh_degree, db, Yb);
+                            sh_colour(a, br.slot[0].gid, Yb, lb);
+                            diag_bounce = (int32_t)br.slot[0].gid;
+                        }
+                        for (int i = 0; i < 3; ++i) c[i] = fmaf(w.albedo[i], lb[i], c[i]);
+                    }
+                }
+            }
+            if (valid) {
+                acc[0] += c[0];
+                acc[1] += c[1];
+                acc[2] += c[2];
+                if (w.samples) {
+                    const int64_t o = ((int64_t)s * w.n_pix + vw.pix_begin + lpix) * 3;
+                    w.samples[o] = diag_cam;
+                    w.samples[o + 1] = diag_bounce;
+                    w.samples[o + 2] = diag_vis;
+                }
+            }
+            __syncwarp();
+        }
+        if (valid) {
+            const float inv_n = 1.0f / (float)a.spp;
+            const int64_t o = 3 * (vw.pix_begin + lpix);
+            a.rgb[o] = acc[0] * inv_n;
+            a.rgb[o + 1] = acc[1] * inv_n;
+            a.rgb[o + 2] = acc[2] * inv_n;
+        }
+    }
+    if (err) atomicOr(a.status, err);
+    if (COUNT) {
+        atomicAdd(w.counters + 0, n_cam);
+        atomicAdd(w.counters + 1, n_shadow);
+        atomicAdd(w.counters + 2, n_bounce);
+        atomicAdd(w.counters + 3, cnt.node_fetch);
+    }
+}
+
+template <int FMT, int STACK, bool COUNT>
+gs_status launch_views(const WaveArgs &w, int threads, cudaStream_t s) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_render_views<FMT, STACK, COUNT>,
+                                                          threads, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "render launch setup");
+    const uint32_t warps_per_block = (uint32_t)threads / 32;
+    uint32_t blocks = (uint32_t)sms * (uint32_t)(per > 0 ? per : 1);
+    const uint32_t max_blocks = (w.total_tiles + warps_per_block - 1) / warps_per_block;
+    if (blocks > max_blocks) blocks = max_blocks;
+    if (blocks == 0) return GS_OK;
+    if ((e = cudaMemsetAsync(w.t.work, 0, sizeof(uint32_t), s)) != cudaSuccess)
+        return cuda_fail(e, "reset work counter");
+    k_render_views<FMT, STACK, COUNT><<<blocks, threads, 0, s>>>(w);
+    return GS_OK;
+}
+
+template <int FMT>
+gs_status launch_views_f(const WaveArgs &w, int threads, int stack, cudaStream_t s) {
+    const bool count = w.counters != nullptr;
+    if (stack == 48)
+        return count ? launch_views<FMT, 48, true>(w, threads, s) : launch_views<FMT, 48, false>(w, threads, s);
+    return count ? launch_views<FMT, 96, true>(w, threads, s) : launch_views<FMT, 96, false>(w, threads, s);
+}
+
+}  // namespace
+
+gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cams,
+                              int n_views, const gs_scene_extras *ex, const gs_trace_params *p,
+                              const gs_launch_options *opt, float *rgb, unsigned long long *counters,
+                              int32_t *samples, cudaStream_t s) {
+    WaveArgs w = {};
+    TraceArgs &a = w.t;
+    a.nodes = b->nodes;
+    a.wide = b->wide;
+    a.prims = b->prims;
+    a.sh = g->sh;
+    a.n_nodes = b->n_nodes;
+    a.sh_degree = g->sh_degree;
+    a.sh_dtype = g->sh_dtype;
+    for (int i = 0; i < 3; ++i) a.bg[i] = p->bg[i];
+    a.key0 = (uint32_t)(p->seed & 0xffffffffu);
+    a.key1 = (uint32_t)(p->seed >> 32);
+    a.stream_tag = p->stream_tag;
+    a.spp = p->spp;
+    a.t_min = p->t_min;
+    a.t_max = p->t_max;
+    const int stack = (opt && opt->stack_entries == 48) ? 48 : 96;
+    a.stack_depth = (p->stack_depth == 0 || p->stack_depth > stack) ? stack : p->stack_depth;
+    a.step_limit = (uint32_t)(b->n_nodes + 8 < (int64_t)kStepLimit ? b->n_nodes + 8 : kStepLimit);
+    a.rgb = rgb;
+    a.status = b->status;
+    a.work = b->status + 1;
+    uint32_t tiles = 0;
+    int64_t pix = 0;
+    for (int v = 0; v < n_views; ++v) {
+        ViewDesc &d = w.views[v];
+        for (int i = 0; i < 3; ++i) {
+            d.eye[i] = cams[v].eye[i];
+            d.look_at[i] = cams[v].look_at[i];
+            d.up[i] = cams[v].up[i];
+        }
+        d.tan_half = (float)tan((double)cams[v].fov_y_deg * 3.14159265358979323846 / 360.0);
+        d.width = cams[v].width;
+        d.height = cams[v].height;
+        d.ray_id_offset = cams[v].ray_id_offset;
+        d.tiles_x = (uint32_t)((cams[v].width + 7) / 8);
+        d.tile_begin = tiles;
+        d.pix_begin = pix;
+        tiles += d.tiles_x * (uint32_t)((cams[v].height + 3) / 4);
+        pix += (int64_t)cams[v].width * cams[v].height;
+    }
+    w.n_views = n_views;
+    w.total_tiles = tiles;
+    w.n_pix = pix;
+    if (ex) {
+        w.n_lights = ex->n_lights;
+        for (int l = 0; l < ex->n_lights; ++l)
+            for (int i = 0; i < 3; ++i) {
+                w.light_pos[l][i] = ex->lights[l].position[i];
+                w.light_int[l][i] = ex->lights[l].intensity[i];
+            }
+        w.has_ground = ex->has_ground;
+        w.ground_y = ex->ground_y;
+        w.ground_half = ex->ground_half_extent;
+        for (int i = 0; i < 3; ++i) {
+            w.albedo[i] = ex->ground_albedo[i];
+            w.albedo_over_pi[i] = (float)((double)ex->ground_albedo[i] / 3.14159265358979323846);
+        }
+        w.bounce = ex->bounce;
+        w.eps = ex->shadow_eps;
+    }
+    w.counters = counters;
+    w.samples = samples;
+    const int threads = opt && opt->block_threads ? opt->block_threads : 128;
+    gs_status st;
+    switch (b->node_format) {
+        case GS_NODES_WIDE4: st = launch_views_f<GS_NODES_WIDE4>(w, threads, stack, s); break;
+        case GS_NODES_WIDE4_Q8: st = launch_views_f<GS_NODES_WIDE4_Q8>(w, threads, stack, s); break;
+        default: st = launch_views_f<GS_NODES_BINARY>(w, threads, stack, s); break;
+    }
+    if (st != GS_OK) return st;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "render launch");
+    return GS_OK;
+}
+
+}  // namespace gsrt

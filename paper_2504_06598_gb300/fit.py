@@ -55,8 +55,10 @@ def fit(steps=200, spp=4, n_hits=1, lr=None, M=500_000, views=16, res=800, seed=
         checkpoint=None, resume=False, log_every=10):
     cloud, cams, true, init, targets, bvh = make_problem(M, views, res, seed)
     params = {k: v.clone().requires_grad_(True) for k, v in init.items()}
-    lrs = lr or {"means": 1e-4, "log_scales": 5e-3, "quats": 1e-3, "opacity_logits": 2e-2,
-                 "sh": 2e-3}
+    # Adam moves each parameter by about lr per step whatever the gradient's
+    # noise, so the rates are kept small enough for 4-sample gradients
+    lrs = lr or {"means": 2e-5, "log_scales": 1e-3, "quats": 2e-4, "opacity_logits": 5e-3,
+                 "sh": 5e-4}
     opt = torch.optim.Adam([{"params": [params[k]], "lr": lrs[k]} for k in KEYS])
     start = 0
     if resume and checkpoint and os.path.exists(checkpoint):
@@ -67,6 +69,18 @@ def fit(steps=200, spp=4, n_hits=1, lr=None, M=500_000, views=16, res=800, seed=
         opt.load_state_dict(ck["opt"])
         start = int(ck["step"])
 
+    def eval_loss(eval_spp=32):
+        """Image loss with many samples and fixed seeds (low noise)."""
+        with torch.no_grad():
+            tot = 0.0
+            for v, cam in enumerate(cams):
+                img = gs.render_differentiable(params["means"], params["log_scales"],
+                                               params["quats"], params["opacity_logits"],
+                                               params["sh"], cloud.sh_degree, cam, bvh=bvh,
+                                               seed=20_000 + v, spp=eval_spp, n_hits=4)
+                tot += float(((img - targets[v]) ** 2).mean())
+            return tot / len(cams)
+
     def param_error():
         with torch.no_grad():
             return {k: float((params[k] - true[k]).abs().mean()) for k in ("means", "log_scales",
@@ -75,6 +89,7 @@ def fit(steps=200, spp=4, n_hits=1, lr=None, M=500_000, views=16, res=800, seed=
     history = []
     t_step = []
     err0 = param_error()
+    eval0 = eval_loss()
     for step in range(start, steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -97,9 +112,10 @@ def fit(steps=200, spp=4, n_hits=1, lr=None, M=500_000, views=16, res=800, seed=
         if checkpoint and (step + 1) % 50 == 0:
             torch.save({"params": {k: params[k].detach() for k in KEYS},
                         "opt": opt.state_dict(), "step": step + 1}, checkpoint)
+    eval1 = eval_loss()
     bvh.sync_status()
     bvh.free()
-    return {"steps": steps, "spp": spp, "n_hits": n_hits, "gaussians": M, "views": views,
+    return {"eval_loss_initial": eval0, "eval_loss_final": eval1, "steps": steps, "spp": spp, "n_hits": n_hits, "gaussians": M, "views": views,
             "res": res, "loss_first": history[0] if history else None,
             "loss_last": history[-1] if history else None, "loss_history": history,
             "param_error_initial": err0, "param_error_final": param_error(),

@@ -83,6 +83,31 @@ class TraceSettings:
     extra: dict = field(default_factory=dict)
 
 
+@dataclass
+class SceneExtras:
+    """Ground quad, point lights and the diffuse bounce of the batched
+    wavefront form (pure data)."""
+    lights: list = field(default_factory=list)  # [(position, intensity), ...]
+    has_ground: bool = False
+    ground_y: float = -1.3
+    ground_half_extent: float = 3.0
+    ground_albedo: tuple = (0.5, 0.5, 0.5)
+    bounce: bool = False
+    shadow_eps: float = 1e-4
+
+
+def ground_and_lights(n_lights: int = 4, seed: int = 0, intensity: float = 4.0) -> SceneExtras:
+    """A ground quad below the unit shell and point lights above it."""
+    rng = np.random.default_rng(seed)
+    lights = []
+    for _ in range(n_lights):
+        a = rng.uniform(0, 2 * np.pi)
+        pos = (float(2.5 * np.cos(a)), float(rng.uniform(2.0, 3.0)), float(2.5 * np.sin(a)))
+        lights.append((pos, (intensity, intensity, intensity)))
+    return SceneExtras(lights=lights, has_ground=True, ground_y=-1.3, ground_half_extent=3.0,
+                       ground_albedo=(0.5, 0.5, 0.5), bounce=True, shadow_eps=1e-4)
+
+
 def _f32(a):
     return np.ascontiguousarray(a, dtype=np.float32)
 
@@ -145,6 +170,30 @@ def orbit_cameras(n_views: int, seed: int = 0, radius: float = 3.0,
         else:
             w, h = fixed_res
         cams.append(Pinhole(width=w, height=h, eye=eye, up=up, ray_id_offset=offset))
+        offset += w * h
+    return cams
+
+
+def wavefront_views(n_views: int = 16, seed: int = 0, radius: float = 3.0,
+                    res_range=((256, 256), (1920, 1080)), fixed_res=None) -> list:
+    """Views of the batched form: eyes on the upper part of a sphere of the
+    given radius (elevation 15-60 degrees, above the ground), looking at the
+    origin, resolutions uniform between the corners of ``res_range``."""
+    rng = np.random.default_rng(seed)
+    cams = []
+    offset = 0
+    for _ in range(n_views):
+        az = rng.uniform(0, 2 * np.pi)
+        el = np.radians(rng.uniform(15.0, 60.0))
+        eye = (float(radius * np.cos(el) * np.cos(az)), float(radius * np.sin(el)),
+               float(radius * np.cos(el) * np.sin(az)))
+        if fixed_res is None:
+            (w0, h0), (w1, h1) = res_range
+            w = int(rng.integers(w0, w1 + 1))
+            h = int(rng.integers(h0, h1 + 1))
+        else:
+            w, h = fixed_res
+        cams.append(Pinhole(width=w, height=h, eye=eye, ray_id_offset=offset))
         offset += w * h
     return cams
 
