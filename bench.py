@@ -53,7 +53,151 @@ def parse():
     ap.add_argument("--case", choices=["trace-1080p"], default=None,
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--n-hits", type=int, default=1, help="N of the profiling case")
+    ap.add_argument("--workload", choices=["shell-1m", "precision-3m", "wavefront-16v"],
+                    default="shell-1m",
+                    help="precision-3m: 3M Gaussians, FP16/BF16 SH, 8-bit 4-wide boxes; "
+                         "wavefront-16v: 16 views, ground, 4 lights, one bounce")
     return ap.parse_args()
+
+
+def run_wavefront(args):
+    """Batched form: the 1M shell above a Lambertian ground quad, 16 views of
+    resolution uniform between 256x256 and 1920x1080, four point lights and
+    one diffuse bounce, 16 spp, N=1. The launch shape and node format come
+    from the autotuner (searched on a 1-spp copy of the workload); each frame
+    (hierarchy rebuild + the persistent render) is replayed from a CUDA graph.
+    The FP32 form and the reduced-precision form (FP16 SH, 8-bit 4-wide
+    boxes) are timed side by side."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_06598_gb300 as gs
+    from paper_2504_06598_gb300 import autotune
+    import scenes
+    spp = 16
+    cloud = scenes.shell_cloud(0, M=M_GAUSS)
+    cams = scenes.wavefront_views(16, seed=0)
+    ex = scenes.ground_and_lights(4, seed=0)
+    total = sum(c.width * c.height for c in cams)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = {"metric": "batched form: rays/s over camera, shadow and bounce rays",
+           "workload": "shell-1M + ground, 16 views 256^2..1080p, 4 lights, 1 bounce",
+           "views": [[c.width, c.height] for c in cams], "pixels": total, "spp": spp,
+           "forms": {}}
+    base = None
+    for name, dt, formats in (("fp32", torch.float32, ("binary", "wide4")),
+                              ("fp16-q8", torch.float16, ("wide4_q8",))):
+        g = gs.Gaussians.from_cloud(cloud, sh_dtype=dt)
+        tune = autotune.autotune(g, cams, ex, spp=1, repeats=1, formats=formats)
+        bvh = gs.build_bvh(g, node_format=tune["node_format"])
+        cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+        gs.render_views(bvh, g, cams, ex, seed=0, spp=spp, counters=cnt,
+                        block_threads=tune["block_threads"], stack_entries=tune["stack_entries"])
+        bvh.sync_status()
+        c = cnt.cpu().numpy().astype(float)
+        frame = gs.FrameGraph(bvh, g, cams, ex, rebuild=True, seed=0, spp=spp,
+                              block_threads=tune["block_threads"],
+                              stack_entries=tune["stack_entries"])
+        st = frame.stream
+        for _ in range(args.warmup):
+            frame.replay()
+        st.synchronize()
+        times = []
+        for k in range(args.steps):
+            with torch.cuda.stream(st):
+                flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            frame.replay()
+            e1.record(st)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        img = frame.rgb.cpu().numpy().astype(np.float64)
+        bvh.sync_status()
+        frame.free()
+        bvh.free()
+        if base is None:
+            base = img
+        ms = float(np.mean(times))
+        rays = c[0] + c[1] + c[2]
+        out["forms"][name] = {
+            "autotuned": {k: tune[k] for k in ("node_format", "stack_entries", "block_threads")},
+            "frame_ms": ms, "camera_rays": c[0], "shadow_rays": c[1], "bounce_rays": c[2],
+            "mrays_per_s": rays / (ms * 1e-3) / 1e6,
+            "camera_mrays_per_s": c[0] / (ms * 1e-3) / 1e6,
+            "rmse_vs_fp32": float(np.sqrt(np.mean((img - base) ** 2))),
+            "max_abs_vs_fp32": float(np.abs(img - base).max())}
+        del g
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
+def run_precision(args):
+    """Precision form: 3M-Gaussian shell (same generator), 1080p, N=1, 64 spp.
+    Every form is timed (hierarchy rebuild + trace, CUDA events, L2 flushed
+    between steps) and compared with the FP32 binary plain form (per-pixel
+    error) and with the FP64 oracle's exact blend on a 4,096-pixel subset."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_06598_gb300 as gs
+    import oracle
+    import scenes
+    M = 3_000_000
+    cloud = scenes.shell_cloud(0, M=M)
+    cam = gs.Camera(W_IMG, H_IMG)
+    npix = W_IMG * H_IMG
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    forms = [("fp32-binary", torch.float32, "binary"), ("fp32-wide4", torch.float32, "wide4"),
+             ("fp16-wide4q8", torch.float16, "wide4_q8"), ("bf16-wide4q8", torch.bfloat16, "wide4_q8")]
+    pix = scenes.pixel_subset(W_IMG, H_IMG, 4096)
+    t0 = time.perf_counter()
+    ref = oracle.render_pinhole(cloud, scenes.default_camera(W_IMG, H_IMG),
+                                scenes.TraceSettings(seed=0, spp=1), pixels=pix, want_hits=False)
+    oracle_s = time.perf_counter() - t0
+    out = {"metric": "precision form: Mrays/s and error at 3M Gaussians 1080p N=1 spp=64",
+           "workload": "shell-3M-1080p", "gaussians": M, "spp": SPP_N1, "n_hits": 1,
+           "oracle_subset_pixels": len(pix), "oracle_seconds": oracle_s, "forms": {}}
+    base_img = None
+    for name, dt, fmt in forms:
+        g = gs.Gaussians.from_cloud(cloud, sh_dtype=dt)
+        bvh = gs.build_bvh(g, node_format=fmt)
+        rgb = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32, device="cuda")
+        for _ in range(args.warmup):
+            bvh.rebuild(g)
+            gs.trace_stochastic(bvh, g, cam, seed=0, spp=SPP_N1, out=rgb)
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record()
+            bvh.rebuild(g)
+            evs[k][1].record()
+            gs.trace_stochastic(bvh, g, cam, seed=0, spp=SPP_N1, out=rgb)
+            evs[k][2].record()
+        torch.cuda.synchronize()
+        bvh.sync_status()
+        info = bvh.info()
+        bvh.free()
+        build = float(np.mean([a.elapsed_time(b) for a, b, _ in evs]))
+        trace = float(np.mean([b.elapsed_time(c) for _, b, c in evs]))
+        img = rgb.cpu().numpy().reshape(-1, 3).astype(np.float64)
+        if base_img is None:
+            base_img = img
+        sub = img[pix]
+        out["forms"][name] = {
+            "node_format": fmt, "sh_dtype": str(dt).replace("torch.", ""),
+            "node_bytes": info["wide_node_bytes"] or info["node_bytes"],
+            "sh_bytes_per_gaussian": 48 * (4 if dt == torch.float32 else 2),
+            "build_ms": build, "trace_ms": trace,
+            "mrays_per_s": npix * SPP_N1 / ((build + trace) * 1e-3) / 1e6,
+            "rmse_vs_blend": float(np.sqrt(np.mean((sub - ref["blend"]) ** 2))),
+            "max_abs_vs_fp32_binary": float(np.abs(img - base_img).max()),
+            "rmse_vs_fp32_binary": float(np.sqrt(np.mean((img - base_img) ** 2))),
+        }
+        del g
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
 
 
 def run_case(args):
@@ -154,7 +298,7 @@ def measured_peak():
 
 def trace_source_hash():
     h = hashlib.sha256()
-    for name in ("trace.cu", "gsrt_internal.cuh"):
+    for name in ("trace.cu", "trace_common.cuh", "gsrt_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2504_06598_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -217,6 +361,12 @@ def main():
     rank, world, local = dist_env()
     if args.case:
         run_case(args)
+        return
+    if args.workload == "precision-3m":
+        run_precision(args)
+        return
+    if args.workload == "wavefront-16v":
+        run_wavefront(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)
