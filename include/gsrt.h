@@ -107,8 +107,17 @@ typedef struct gs_pinhole {
  *   t_min, t_max  valid ray range, candidates need t_min < t < t_max
  *   bg            background colour of samples with no accepted hit
  *   depth_mode    0: depth is the mean of the 1D Gaussian (Sec. 3.1)
+ *                 1: depth is the centre projected on the camera's forward
+ *                    axis (Sec. 4.1); alpha stays the 1D peak
+ *                    (gs_trace_stochastic only; this depth is not a ray
+ *                    parameter, so accepted hits do not clip the traversal)
  *   stack_depth   traversal stack entries per ray, 1..96 (0 = 96)
  *   stream_tag    fourth Philox counter word, separates ray streams
+ *   rng_mode      0: keyed Philox (above); 1: the trigonometric hash of
+ *                 the hit point of Eq. 8-9, moved per sample by
+ *                 1e-3 * frac(s * (0.8191725134, 0.6710436067,
+ *                 0.5497004779)) - 5e-4 (gs_trace_stochastic only; float32,
+ *                 not reproducible bit for bit)
  *   counters      optional device uint64[7], incremented by the launch:
  *                 {nodes entered by each ray's own traversal, Gaussians
  *                 tested (Alg. 1 runs), Philox calls, rays (pixels),
@@ -125,6 +134,7 @@ typedef struct gs_trace_params {
     int32_t depth_mode;
     int32_t stack_depth;
     uint32_t stream_tag;
+    int32_t rng_mode;
     unsigned long long *counters;
 } gs_trace_params;
 

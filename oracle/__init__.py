@@ -62,7 +62,8 @@ class _Pinhole(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("spp", C.c_int32), ("n_hits", C.c_int32),
                 ("t_min", C.c_double), ("t_max", C.c_double), ("bg", C.c_double * 3),
-                ("stream_tag", C.c_uint32), ("pad", C.c_int32)]
+                ("stream_tag", C.c_uint32), ("depth_mode", C.c_int32), ("rng_mode", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 def _load():
@@ -93,6 +94,8 @@ def _load():
             lib.orc_grad_pinhole.argtypes = [P, P, P, C.c_int64, P, P, C.c_int, P, P, P, P, P,
                                              C.c_int]
             lib.orc_bounce_dir.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, P]
+            lib.orc_hash_xi.restype = C.c_double
+            lib.orc_hash_xi.argtypes = [P, C.c_uint32]
             lib.orc_render_scene.restype = C.c_int
             lib.orc_render_scene.argtypes = [P, P, C.c_int32, P, P, C.c_int64, P, P, P, P, C.c_int]
             lib.orc_render_rays.restype = C.c_int
@@ -145,6 +148,8 @@ def _params(st):
     p.t_max = float(st.t_max)
     p.bg[:] = [float(v) for v in st.bg]
     p.stream_tag = int(st.stream_tag)
+    p.depth_mode = int(getattr(st, "depth_mode", 0))
+    p.rng_mode = int(getattr(st, "rng_mode", 0))
     return p
 
 
@@ -397,3 +402,9 @@ def bounce_dir(seed, ray_id, sample):
     d = np.zeros(3, np.float32)
     lib.orc_bounce_dir(int(seed), int(ray_id), int(sample), _ptr(d))
     return d
+
+
+def hash_xi(p, sample):
+    """The trigonometric hash draw (Eq. 8-9) of hit position p for a sample."""
+    q = _c(p, np.float64)
+    return float(_load().orc_hash_xi(_ptr(q), int(sample)))

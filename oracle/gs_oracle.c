@@ -83,6 +83,8 @@ typedef struct {
     double t_max;
     double bg[3];
     uint32_t stream_tag;
+    int32_t depth_mode; /* 0: mean of the 1D Gaussian; 1: projected centre */
+    int32_t rng_mode;   /* 0: Philox; 1: trigonometric hash of the hit point */
     int32_t pad;
 } orc_params;
 
@@ -121,6 +123,30 @@ double orc_xi(uint64_t seed, uint32_t ray_id, uint32_t gid, uint32_t sample, uin
     orc_philox4x32_10(ctr, key, u);
     return (double)(u[sample & 3u] >> 8) * (1.0 / 16777216.0);
 }
+
+/* Trigonometric hash of a hit position (Sec. 4.2, Eq. 8-9):
+ *   r1(q) = fract(b1 sin(a1 q)), r2(q) = fract(b2 sin(a2^T q)),
+ *   xi(p) = r2(p_xy + r1(p_z)), a1 = 91.3458, b1 = 47453.5453,
+ *   a2 = (12.9898, 78.233), b2 = 43758.5453 (both entries equal, so both
+ *   components of r2 are equal; the first is used).
+ * The paper makes the draws change between frames by jittering the camera
+ * rays; here the rays are fixed, so sample s hashes p + delta_s, with
+ * delta_s = 1e-3 * (frac(s c1), frac(s c2), frac(s c3)) - 5e-4 from the
+ * additive recurrence with c = (0.8191725134, 0.6710436067, 0.5497004779). */
+static double fract_d(double x) { return x - floor(x); }
+
+double orc_hash_xi(const double p[3], uint32_t sample)
+{
+    const double c[3] = {0.8191725134, 0.6710436067, 0.5497004779};
+    double q[3];
+    for (int i = 0; i < 3; ++i) q[i] = p[i] + 1e-3 * fract_d((double)sample * c[i]) - 5e-4;
+    double r1 = fract_d(47453.5453 * sin(91.3458 * q[2]));
+    double x = q[0] + r1, y = q[1] + r1;
+    return fract_d(43758.5453 * sin(12.9898 * x + 78.233 * y));
+}
+
+/* Camera forward axis of a pinhole, float32 as in orc_camera_ray. */
+static void cam_forward(const float eye[3], const float at[3], double f[3]);
 
 /* ------------------------------------------------------------------ */
 /* Parameter activation (Eq. 1)                                          */
@@ -321,6 +347,14 @@ static void cross_f(const float a[3], const float b[3], float c[3])
     p = a[0] * b[1]; m = a[1] * b[0]; c[2] = p - m;
 }
 
+static void cam_forward(const float eye[3], const float at[3], double f[3])
+{
+    float ff[3];
+    for (int i = 0; i < 3; ++i) ff[i] = at[i] - eye[i];
+    normalise_f(ff);
+    for (int i = 0; i < 3; ++i) f[i] = (double)ff[i];
+}
+
 void orc_camera_ray(const orc_pinhole *cam, int32_t x, int32_t y, double o[3], double d[3],
                     uint32_t *ray_id)
 {
@@ -460,8 +494,11 @@ static void cand_push(cand_list *L, const orc_cand *c)
     L->v[L->n++] = *c;
 }
 
-static void collect(const orc_scene *sc, const orc_gauss *act, const double o[3], const double d[3],
-                    double t_min, double t_max, cand_list *L)
+/* fwd != NULL: depth is the Gaussian centre projected on the camera's
+ * forward axis (Sec. 4.1); alpha stays the peak of the 1D Gaussian. */
+static void collect_mode(const orc_scene *sc, const orc_gauss *act, const double o[3],
+                         const double d[3], double t_min, double t_max, const double *fwd,
+                         cand_list *L)
 {
     double Y[16];
     orc_sh_basis(sc->sh_degree, d, Y);
@@ -469,6 +506,9 @@ static void collect(const orc_scene *sc, const orc_gauss *act, const double o[3]
     for (int64_t g = 0; g < sc->M; ++g) {
         double t, q;
         gauss1d(&act[g], o, d, &t, &q);
+        if (fwd)
+            t = (act[g].mu[0] - o[0]) * fwd[0] + (act[g].mu[1] - o[1]) * fwd[1] +
+                (act[g].mu[2] - o[2]) * fwd[2];
         if (!(t > t_min && t < t_max)) continue; /* Alg. 1 range test */
         if (!(q <= ORC_S2)) continue;            /* Eq. 2 negligibility */
         orc_cand c;
@@ -479,6 +519,12 @@ static void collect(const orc_scene *sc, const orc_gauss *act, const double o[3]
         sh_colour(sc, g, Y, c.rgb);
         cand_push(L, &c);
     }
+}
+
+static void collect(const orc_scene *sc, const orc_gauss *act, const double o[3], const double d[3],
+                    double t_min, double t_max, cand_list *L)
+{
+    collect_mode(sc, act, o, d, t_min, t_max, NULL, L);
 }
 
 static orc_gauss *activate_all(const orc_scene *sc)
@@ -514,17 +560,24 @@ int64_t orc_ray_candidates(const orc_scene *sc, const double o[3], const double 
 /* One ray: exact blend (Eq. 3) and S = spp*N estimator samples (Eq. 6),
  * averaged (Eq. 7). Sample s uses draw xi(seed, ray_id, gid, s). */
 static void trace_one(const orc_scene *sc, const orc_gauss *act, const orc_params *p,
-                      const double o[3], const double d[3], uint32_t ray_id, cand_list *L,
-                      double blend[3], double *blend2, double est[3], int32_t *hit_id,
-                      double *hit_t)
+                      const double o[3], const double d[3], uint32_t ray_id, const double *fwd,
+                      cand_list *L, double blend[3], double *blend2, double est[3],
+                      int32_t *hit_id, double *hit_t)
 {
-    collect(sc, act, o, d, p->t_min, p->t_max, L);
+    collect_mode(sc, act, o, d, p->t_min, p->t_max, p->depth_mode == 1 ? fwd : NULL, L);
     int64_t S = (int64_t)p->spp * p->n_hits;
     double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t s = 0; s < S; ++s) {
         int64_t win = -1;
         for (int64_t i = 0; i < L->n; ++i) {
-            double xi = orc_xi(p->seed, ray_id, (uint32_t)L->v[i].gid, (uint32_t)s, p->stream_tag);
+            double xi;
+            if (p->rng_mode == 1) {
+                double ph[3];
+                for (int k = 0; k < 3; ++k) ph[k] = o[k] + L->v[i].t * d[k];
+                xi = orc_hash_xi(ph, (uint32_t)s);
+            } else {
+                xi = orc_xi(p->seed, ray_id, (uint32_t)L->v[i].gid, (uint32_t)s, p->stream_tag);
+            }
             if (!(xi < L->v[i].alpha)) continue; /* Eq. 4: accepted with probability alpha */
             if (win < 0 || lex_less(L->v[i].t, L->v[i].gid, L->v[win].t, L->v[win].gid)) win = i;
         }
@@ -579,7 +632,9 @@ int orc_render_pinhole(const orc_scene *sc, const orc_pinhole *cam, const orc_pa
             double o[3], d[3];
             uint32_t rid;
             orc_camera_ray(cam, x, y, o, d, &rid);
-            trace_one(sc, act, p, o, d, rid, &L, blend ? blend + 3 * i : 0,
+            double fwd[3];
+            cam_forward(cam->eye, cam->look_at, fwd);
+            trace_one(sc, act, p, o, d, rid, fwd, &L, blend ? blend + 3 * i : 0,
                       blend2 ? blend2 + 3 * i : 0, est ? est + 3 * i : 0,
                       hit_id ? hit_id + S * i : 0, hit_t ? hit_t + S * i : 0);
             if (n_valid) n_valid[i] = L.n;
@@ -619,7 +674,7 @@ int orc_render_rays(const orc_scene *sc, const orc_params *p, int64_t n_rays, co
                 o[k] = (double)origins[3 * i + k];
                 d[k] = (double)dirs[3 * i + k];
             }
-            trace_one(sc, act, p, o, d, ray_ids[i], &L, blend ? blend + 3 * i : 0,
+            trace_one(sc, act, p, o, d, ray_ids[i], NULL, &L, blend ? blend + 3 * i : 0,
                       blend2 ? blend2 + 3 * i : 0, est ? est + 3 * i : 0,
                       hit_id ? hit_id + S * i : 0, hit_t ? hit_t + S * i : 0);
             if (n_valid) n_valid[i] = L.n;

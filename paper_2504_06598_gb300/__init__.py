@@ -54,7 +54,7 @@ class _TraceParams(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("spp", C.c_int32), ("n_hits", C.c_int32),
                 ("t_min", C.c_float), ("t_max", C.c_float), ("bg", C.c_float * 3),
                 ("depth_mode", C.c_int32), ("stack_depth", C.c_int32),
-                ("stream_tag", C.c_uint32), ("counters", C.c_void_p)]
+                ("stream_tag", C.c_uint32), ("rng_mode", C.c_int32), ("counters", C.c_void_p)]
 
 
 class _BvhInfo(C.Structure):
@@ -194,7 +194,8 @@ class Camera:
 
 
 def _params(seed=0, spp=1, n_hits=1, t_min=0.0, t_max=float("inf"), bg=(0.0, 0.0, 0.0),
-            stack_depth=0, stream_tag=0, counters=None) -> _TraceParams:
+            stack_depth=0, stream_tag=0, counters=None, depth_mode=0,
+            rng_mode=0) -> _TraceParams:
     p = _TraceParams()
     p.seed = int(seed)
     p.spp = int(spp)
@@ -202,9 +203,10 @@ def _params(seed=0, spp=1, n_hits=1, t_min=0.0, t_max=float("inf"), bg=(0.0, 0.0
     p.t_min = float(t_min)
     p.t_max = float(t_max)
     p.bg[:] = [float(v) for v in bg]
-    p.depth_mode = 0
+    p.depth_mode = int(depth_mode)
     p.stack_depth = int(stack_depth)
     p.stream_tag = int(stream_tag)
+    p.rng_mode = int(rng_mode)
     p.counters = None if counters is None else counters.data_ptr()
     return p
 
@@ -291,7 +293,8 @@ def build_bvh(g: Gaussians, stream=None, node_format="binary") -> Bvh:
 
 def trace_stochastic(bvh: Bvh, g: Gaussians, cam, seed=0, spp=1, n_hits=1, t_min=0.0,
                      t_max=float("inf"), bg=(0.0, 0.0, 0.0), stack_depth=0, stream_tag=0,
-                     want_hits=False, counters=None, out=None, stream=None):
+                     want_hits=False, counters=None, out=None, stream=None, depth_mode=0,
+                     rng_mode=0):
     """``gs_trace_stochastic``: render one pinhole view.
 
     Returns ``rgb`` [H, W, 3] float32 (and ``hit_id``, ``hit_t`` of shape
@@ -306,7 +309,8 @@ def trace_stochastic(bvh: Bvh, g: Gaussians, cam, seed=0, spp=1, n_hits=1, t_min
         hit_t = torch.empty((spp, n_hits, H, W), dtype=torch.float32, device=dev)
     gs = g.struct()
     cs = cam.struct()
-    ps = _params(seed, spp, n_hits, t_min, t_max, bg, stack_depth, stream_tag, counters)
+    ps = _params(seed, spp, n_hits, t_min, t_max, bg, stack_depth, stream_tag, counters,
+                 depth_mode, rng_mode)
     _check(lib().gs_trace_stochastic(
         bvh.handle, C.byref(gs), C.byref(cs), C.byref(ps), C.c_void_p(rgb.data_ptr()),
         None if hit_id is None else C.c_void_p(hit_id.data_ptr()),

@@ -309,7 +309,10 @@ static gs_status check_trace_args(const gs_bvh *b, const gs_gaussians *g, const 
         return fail(GS_ERR_INVALID_ARG, "spp * n_hits too large");
     if (p->stack_depth < 0 || p->stack_depth > kMaxStack)
         return fail(GS_ERR_INVALID_ARG, "stack_depth=%d not in 0..%d", p->stack_depth, kMaxStack);
-    if (p->depth_mode != 0) return fail(GS_ERR_INVALID_ARG, "depth_mode=%d unsupported", p->depth_mode);
+    if (p->depth_mode != 0 && p->depth_mode != 1)
+        return fail(GS_ERR_INVALID_ARG, "depth_mode=%d unsupported", p->depth_mode);
+    if (p->rng_mode != 0 && p->rng_mode != 1)
+        return fail(GS_ERR_INVALID_ARG, "rng_mode=%d unsupported", p->rng_mode);
     if (isnan(p->t_min) || isnan(p->t_max) || !(p->t_min < p->t_max))
         return fail(GS_ERR_INVALID_ARG, "need t_min < t_max");
     return GS_OK;
@@ -339,6 +342,8 @@ gs_status gs_trace_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pin
                             float *d_sh, void *stream) {
     gs_status st = check_trace_args(b, g, cam, p);
     if (st != GS_OK) return st;
+    if (p->depth_mode != 0 || p->rng_mode != 0)
+        return fail(GS_ERR_INVALID_ARG, "gradients need depth_mode 0 and rng_mode 0");
     if (!d_rgb || !d_means || !d_log_scales || !d_quats || !d_opacity_logits || !d_sh)
         return fail(GS_ERR_INVALID_ARG, "d_rgb and every gradient array are required");
     if (((uintptr_t)g->quats & 15u) != 0)
@@ -376,6 +381,8 @@ gs_status gs_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_pinho
     gs_status st = check_trace_args(b, g, &cams[0], p);
     if (st != GS_OK) return st;
     if (p->n_hits != 1) return fail(GS_ERR_INVALID_ARG, "the wavefront form takes n_hits = 1");
+    if (p->depth_mode != 0 || p->rng_mode != 0)
+        return fail(GS_ERR_INVALID_ARG, "the wavefront form needs depth_mode 0 and rng_mode 0");
     for (int v = 0; v < n_views; ++v)
         if ((st = check_camera(&cams[v])) != GS_OK) return st;
     for (int v = 0; v < n_views; ++v)

@@ -193,6 +193,18 @@ gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole 
     a.counters = p->counters;
     a.status = b->status;
     a.work = b->status + 1;
+    a.depth_mode = p->depth_mode;
+    a.rng_mode = p->rng_mode;
+    {
+        // camera forward axis, float32 normalise as for the camera rays
+        float f[3];
+        for (int i = 0; i < 3; ++i) f[i] = cam->look_at[i] - cam->eye[i];
+        float n2 = f[0] * f[0];
+        n2 = n2 + f[1] * f[1];
+        n2 = n2 + f[2] * f[2];
+        const float n = sqrtf(n2);
+        for (int i = 0; i < 3; ++i) a.fwd[i] = f[i] / n;
+    }
     const bool count = p->counters != nullptr;
     gs_status st;
     switch (p->n_hits) {

@@ -40,6 +40,9 @@ struct TraceArgs {
     unsigned long long *counters;
     uint32_t *status;
     uint32_t *work;  // tile counter of the persistent launch
+    int depth_mode;  // 0: 1D mean; 1: centre projected on fwd (camera rays)
+    int rng_mode;    // 0: Philox; 1: trigonometric hash of the hit point
+    float fwd[3];    // camera forward axis (depth_mode 1)
     // backward pass only
     const float *d_rgb;        // [H][W][3] dLoss/d(pixel mean)
     const float *log_scales;   // raw parameters, for the scale and rotation
@@ -244,6 +247,21 @@ __device__ __forceinline__ void update_clip(Ray<N> &r, float t_max) {
     r.t_far = far + fabsf(far) * 0x1p-19f;
 }
 
+// Trigonometric hash draw of Eq. 8-9 at hit point p for sample s (an
+// alternative to Philox): xi = fract(b2 sin(a2 . (p_xy + r1(p_z)))), with
+// r1(q) = fract(b1 sin(a1 q)), after moving p by a per-sample offset from
+// the additive recurrence (fixed rays give no per-frame jitter here).
+__device__ __forceinline__ float fract_f(float x) { return x - floorf(x); }
+
+__device__ __forceinline__ float hash_xi(const float p[3], uint32_t s) {
+    const float c[3] = {0.8191725134f, 0.6710436067f, 0.5497004779f};
+    float q[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) q[i] = p[i] + 1e-3f * fract_f((float)s * c[i]) - 5e-4f;
+    const float r1 = fract_f(47453.5453f * sinf(91.3458f * q[2]));
+    return fract_f(43758.5453f * sinf(12.9898f * (q[0] + r1) + 78.233f * (q[1] + r1)));
+}
+
 // Alg. 1 for primitive record idx against all N slots of the current pass.
 template <int N, bool COUNT>
 __device__ __forceinline__ void intersect(const TraceArgs &a, Ray<N> &r, uint32_t idx, int pass,
@@ -277,14 +295,23 @@ __device__ __forceinline__ void intersect(const TraceArgs &a, Ray<N> &r, uint32_
     const float wd = fmaf(mw[0], md[0], fmaf(mw[1], md[1], mw[2] * md[2]));
     const float inv_dd = 1.0f / dd;
     const float tau = -wd * inv_dd;
-    const float t = tc + tau;
+    float t = tc + tau;
+    // depth key (tc, tau); the projected-centre depth uses (centre, 0)
+    float key_tc = tc, key_tau = tau;
+    if (a.depth_mode == 1) {
+        const float hf = fmaf(h[0], a.fwd[0], fmaf(h[1], a.fwd[1], h[2] * a.fwd[2]));
+        const float lf = fmaf(l[0], a.fwd[0], fmaf(l[1], a.fwd[1], l[2] * a.fwd[2]));
+        t = -(hf + lf);
+        key_tc = t;
+        key_tau = 0.0f;
+    }
     // Alg. 1 range test; t_far only prunes hits behind every slot
     if (!(t > r.t_min) || !(t < r.t_max) || !(t <= r.t_far)) return;
     bool closer[N];
     bool any = false;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-        closer[k] = lex_closer(tc, tau, gid, r.slot[k]);
+        closer[k] = lex_closer(key_tc, key_tau, gid, r.slot[k]);
         any |= closer[k];
     }
     if (!any) return;
@@ -300,9 +327,27 @@ __device__ __forceinline__ void intersect(const TraceArgs &a, Ray<N> &r, uint32_
     const float q = fmaxf(ww - wd2 * wd2 * inv_dd, 0.0f);
     if (!(q <= kS2)) return;
     const float alpha = p0.w * expf(-0.5f * q);
+    const uint32_t s0 = (uint32_t)pass * N;
+    if (a.rng_mode == 1) {
+        float ph[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) ph[i] = fmaf(t, r.d[i], r.o[i]);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            if (!closer[k]) continue;
+            if (hash_xi(ph, s0 + k) < alpha) {
+                r.slot[k].t = t;
+                r.slot[k].tc = key_tc;
+                r.slot[k].tau = key_tau;
+                r.slot[k].gid = gid;
+            }
+        }
+        update_clip(r, r.t_max);
+        if (a.depth_mode == 1) r.t_far = r.t_max;
+        return;
+    }
     // Eq. 4: one Philox call serves four consecutive samples
     uint4 u0 = make_uint4(0, 0, 0, 0), u1 = make_uint4(0, 0, 0, 0);
-    const uint32_t s0 = (uint32_t)pass * N;
     u0 = philox10(make_uint4(r.ray_id, gid, s0 >> 2, r.stream_tag), a.key0, a.key1);
     if (N == 8) u1 = philox10(make_uint4(r.ray_id, gid, (s0 >> 2) + 1, r.stream_tag), a.key0, a.key1);
     if (COUNT) n_draws += 1 + (N == 8);
@@ -313,13 +358,16 @@ __device__ __forceinline__ void intersect(const TraceArgs &a, Ray<N> &r, uint32_
         const uint32_t bits = (N == 8 && k >= 4) ? pick(u1, s & 3) : pick(u0, s & 3);
         if (lane_to_unit(bits) < alpha) {
             r.slot[k].t = t;
-            r.slot[k].tc = tc;
-            r.slot[k].tau = tau;
+            r.slot[k].tc = key_tc;
+            r.slot[k].tau = key_tau;
             r.slot[k].gid = gid;
         }
     }
     update_clip(r, r.t_max);
     if (r.any_hit && r.slot[0].gid != 0xffffffffu) r.t_far = -INFINITY;  // visibility known
+    // A projected-centre depth is not a ray parameter, so it cannot clip the
+    // box tests: every box on the ray stays open and order is decided here.
+    if (a.depth_mode == 1) r.t_far = r.t_max;
 }
 
 // Slab test of one child box against [t_min, t_far].

@@ -80,6 +80,7 @@ class TraceSettings:
     bg: tuple = (0.0, 0.0, 0.0)
     stream_tag: int = 0
     depth_mode: int = 0  # 0: mean of the 1D Gaussian, 1: projected centre
+    rng_mode: int = 0    # 0: Philox, 1: trigonometric hash of the hit position
     extra: dict = field(default_factory=dict)
 
 
