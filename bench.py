@@ -385,9 +385,10 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
+    from paper_2504_06598_gb300 import parallel
     cloud = scenes.shell_cloud(0, M=M_GAUSS)
     npix = W_IMG * H_IMG
-    cam = gs.Camera(W_IMG, H_IMG, ray_id_offset=rank * npix)
+    cam = parallel.rank_view(gs.Camera(W_IMG, H_IMG), rank)
     g = gs.Gaussians.from_cloud(cloud)
     bvh = gs.build_bvh(g)
     bvh.sync_status()
@@ -434,10 +435,8 @@ def main():
         trace = np.array([b.elapsed_time(c) for _, b, c in evs])
         res = {"step_ms": float(np.mean(build + trace)), "build_ms": float(np.mean(build)),
                "trace_ms": float(np.mean(trace)), "clocks": clk.summary()}
-        if dist:
-            t = torch.tensor([res["step_ms"], res["trace_ms"]], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            res["step_ms"], res["trace_ms"] = float(t[0]), float(t[1])
+        res["step_ms"], res["trace_ms"] = parallel.max_over_ranks(
+            [res["step_ms"], res["trace_ms"]], device=dev)
         return res
 
     bvh.sync_status()
@@ -466,11 +465,7 @@ def main():
         if k >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
     bvh.sync_status()
-    e2e_mean = float(np.mean(e2e_ms))
-    if dist:
-        t = torch.tensor([e2e_mean], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_mean = float(t[0])
+    e2e_mean = parallel.max_over_ranks([float(np.mean(e2e_ms))], device=dev)[0]
 
     rays_step = npix * SPP_N1 * world
     value = rays_step / (r1["step_ms"] * 1e-3) / 1e6
