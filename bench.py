@@ -485,11 +485,17 @@ def main():
         warp = (info["node_bytes"] * v["node_fetch"] + info["prim_bytes"] * v["prim_fetch"]
                 + sh_bytes * v["shaded"] + 12 * npix)
         ach = alg / (trace_ms * 1e-3) / 1e9
-        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": recorded_traffic(n_hits),
-                "alg_bytes_per_launch": alg, "warp_request_bytes_per_launch": warp,
-                "warp_request_gbs": warp / (trace_ms * 1e-3) / 1e9,
-                "peak_kind": peak_kind, "kernel": "k_trace<%d>" % n_hits}
+        traffic = recorded_traffic(n_hits)
+        out = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+               "frac": ach / peak, "traffic": traffic,
+               "alg_bytes_per_launch": alg, "warp_request_bytes_per_launch": warp,
+               "warp_request_gbs": warp / (trace_ms * 1e-3) / 1e9,
+               "peak_kind": peak_kind, "kernel": "k_trace<%d>" % n_hits}
+        if traffic is not None:
+            # what DRAM actually moved (ncu counters) over this run's duration
+            out["dram_gbs"] = traffic / (trace_ms * 1e-3) / 1e9
+            out["dram_frac"] = out["dram_gbs"] / peak
+        return out
 
     line = {
         "metric": "Mrays/s at 1M Gaussians 1080p (N=1,4); RMSE vs exact blend at equal time",
