@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--case", choices=["trace-1080p"], default=None,
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--n-hits", type=int, default=1, help="N of the profiling case")
+    ap.add_argument("--case-spp", type=int, default=1, help="spp of the profiling case")
     ap.add_argument("--workload", choices=["shell-1m", "precision-3m", "wavefront-16v"],
                     default="shell-1m",
                     help="precision-3m: 3M Gaussians, FP16/BF16 SH, 8-bit 4-wide boxes; "
@@ -201,8 +202,9 @@ def run_precision(args):
 
 
 def run_case(args):
-    """Profiling case: the 1M-Gaussian shell, the 1920x1080 view, spp=1,
-    traced twice (warm-up launch, then the launch to capture)."""
+    """Profiling case: the 1M-Gaussian shell, the 1920x1080 view, spp=1
+    (or --case-spp), traced twice (warm-up launch, then the launch to
+    capture)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -213,7 +215,7 @@ def run_case(args):
     bvh = gs.build_bvh(g)
     cam = gs.Camera(W_IMG, H_IMG)
     for _ in range(2):
-        gs.trace_stochastic(bvh, g, cam, seed=0, spp=1, n_hits=args.n_hits)
+        gs.trace_stochastic(bvh, g, cam, seed=0, spp=args.case_spp, n_hits=args.n_hits)
     bvh.sync_status()
     torch.cuda.synchronize()
     bvh.free()

@@ -262,7 +262,12 @@ template <int N>
 __global__ void __launch_bounds__(kThreads) k_backward(const TraceArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;
-    const uint32_t tiles_x = (a.width + 7) / 8, tiles_y = (a.height + 3) / 4;
+    // pixels x samples per warp as in the forward trace
+    const int lg = a.lpp_log2, L = 1 << lg;
+    const int tw_lg = tile_w_log2(lg), th_lg = 5 - lg - tw_lg;
+    const int sub = lane & (L - 1), pl = lane >> lg;
+    const uint32_t tiles_x = (uint32_t)((a.width + (1 << tw_lg) - 1) >> tw_lg);
+    const uint32_t tiles_y = (uint32_t)((a.height + (1 << th_lg) - 1) >> th_lg);
     const uint32_t n_tiles = tiles_x * tiles_y;
     const int K = (a.sh_degree + 1) * (a.sh_degree + 1);
     uint32_t stack[kMaxStack];
@@ -274,8 +279,8 @@ __global__ void __launch_bounds__(kThreads) k_backward(const TraceArgs a) {
         if (lane == 0) tile = atomicAdd(a.work, 1u);
         tile = __shfl_sync(kAll, tile, 0);
         if (tile >= n_tiles) break;
-        const int x = (int)((tile % tiles_x) * 8 + (lane & 7));
-        const int y = (int)((tile / tiles_x) * 4 + (lane >> 3));
+        const int x = (int)(((tile % tiles_x) << tw_lg) + (pl & ((1 << tw_lg) - 1)));
+        const int y = (int)(((tile / tiles_x) << th_lg) + (pl >> tw_lg));
         const bool valid = x < a.width && y < a.height;
         const int64_t pix = valid ? (int64_t)y * a.width + x : 0;
         Ray<N> r;
@@ -295,11 +300,14 @@ __global__ void __launch_bounds__(kThreads) k_backward(const TraceArgs a) {
         float g[3] = {0.0f, 0.0f, 0.0f};
         if (valid)
             for (int ch = 0; ch < 3; ++ch) g[ch] = a.d_rgb[3 * pix + ch] * inv_s;
-        for (int pass = 0; pass < a.spp; ++pass) {
+        const int n_rounds = (a.spp + L - 1) >> lg;
+        for (int j = 0; j < n_rounds; ++j) {
+            const int pass = (j << lg) + sub;
+            const bool live = valid && pass < a.spp;
 #pragma unroll
             for (int k = 0; k < N; ++k) r.slot[k] = Slot{INFINITY, INFINITY, 0.0f, 0xffffffffu};
             update_clip(r, a.t_max);
-            if (!valid) r.t_far = -INFINITY;
+            if (!live) r.t_far = -INFINITY;
             if (a.n_nodes == 0) continue;
             // 1) the forward traversal: same keys, same winners
             traverse_packet<N, false>(a, r, pass, stack, stack_t, err, cnt);
@@ -307,7 +315,7 @@ __global__ void __launch_bounds__(kThreads) k_backward(const TraceArgs a) {
             float ck[N][3];
 #pragma unroll
             for (int k = 0; k < N; ++k) {
-                if (valid && r.slot[k].gid != 0xffffffffu) {
+                if (live && r.slot[k].gid != 0xffffffffu) {
                     float raw[3];
                     sh_colour_raw(a, r.slot[k].gid, Y, raw);
                     const int64_t base = (int64_t)r.slot[k].gid * K * 3;
@@ -323,7 +331,7 @@ __global__ void __launch_bounds__(kThreads) k_backward(const TraceArgs a) {
             }
             // 3) every Gaussian in front of a winner
             update_clip(r, a.t_max);
-            if (!valid) r.t_far = -INFINITY;
+            if (!live) r.t_far = -INFINITY;
             enumerate_packet<N>(a, r, ck, g, Y, stack, stack_t, err);
             __syncwarp();
         }
@@ -338,7 +346,9 @@ gs_status launch_backward_n(const TraceArgs &a, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_backward<N>, kThreads, 0);
     if (e != cudaSuccess) return cuda_fail(e, "backward launch setup");
-    const uint32_t tiles = (uint32_t)(((a.width + 7) / 8) * ((a.height + 3) / 4));
+    const int tw_lg = tile_w_log2(a.lpp_log2), th_lg = 5 - a.lpp_log2 - tw_lg;
+    const uint32_t tiles = (uint32_t)(((a.width + (1 << tw_lg) - 1) >> tw_lg) *
+                                      ((a.height + (1 << th_lg) - 1) >> th_lg));
     uint32_t blocks = (uint32_t)sms * (uint32_t)(per > 0 ? per : 1);
     const uint32_t max_blocks = (tiles + kThreads / 32 - 1) / (kThreads / 32);
     if (blocks > max_blocks) blocks = max_blocks;
@@ -381,6 +391,7 @@ gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinho
     a.step_limit = (uint32_t)(b->n_nodes + 8 < (int64_t)kStepLimit ? b->n_nodes + 8 : kStepLimit);
     a.status = b->status;
     a.work = b->status + 1;
+    a.lpp_log2 = lanes_per_pixel_log2(p->spp);
     a.d_rgb = d_rgb;
     a.log_scales = g->log_scales;
     a.quats = g->quats;

@@ -1,7 +1,11 @@
 // trace.cu -- stochastic ray tracing of transparent Gaussians on sm_103a.
 //
-// One thread per pixel, one warp per 8x4 pixel tile, traversing as a packet
-// (see traverse_packet). Each pass is one traversal of the hierarchy
+// One warp per tile of pixels, traversing as a packet (see traverse_packet).
+// With spp >= 2 the 32 lanes are split into pixels x samples: the L lanes of
+// one pixel trace passes sub, sub + L, ... of the same camera ray (L the
+// largest power of two not above spp, at most 32), so a packet shares its
+// ray and differs only in the random draws and the clip they cause; at
+// spp = 1 the tile is 8x4 pixels. Each pass is one traversal of the hierarchy
 // (Sec. 3.2) keeping N closest accepted intersections (Sec. 3.5). At every
 // leaf the intersection routine of Alg. 1 runs:
 //   t    mean of the 1D Gaussian along the ray (Sec. 3.1)
@@ -32,14 +36,18 @@
 namespace gsrt {
 namespace {
 
-// Persistent kernel: each warp repeatedly takes the next 8x4 pixel tile
-// (one atomic per tile, so the tail of the launch stays balanced), then
-// runs all passes of its 32 pixels.
+// Persistent kernel: each warp repeatedly takes the next tile (one atomic
+// per tile, so the tail of the launch stays balanced), then runs all passes
+// of its pixels.
 template <int N, bool COUNT, int FMT>
 __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;
-    const uint32_t tiles_x = (a.width + 7) / 8, tiles_y = (a.height + 3) / 4;
+    const int lg = a.lpp_log2, L = 1 << lg;
+    const int tw_lg = tile_w_log2(lg), th_lg = 5 - lg - tw_lg;
+    const int sub = lane & (L - 1), pl = lane >> lg;
+    const uint32_t tiles_x = (uint32_t)((a.width + (1 << tw_lg) - 1) >> tw_lg);
+    const uint32_t tiles_y = (uint32_t)((a.height + (1 << th_lg) - 1) >> th_lg);
     const uint32_t n_tiles = tiles_x * tiles_y;
     const int64_t npix = (int64_t)a.width * a.height;
     uint32_t stack[kMaxStack];
@@ -52,8 +60,8 @@ __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
         if (lane == 0) tile = atomicAdd(a.work, 1u);
         tile = __shfl_sync(kAll, tile, 0);
         if (tile >= n_tiles) break;
-        const int x = (int)((tile % tiles_x) * 8 + (lane & 7));
-        const int y = (int)((tile / tiles_x) * 4 + (lane >> 3));
+        const int x = (int)(((tile % tiles_x) << tw_lg) + (pl & ((1 << tw_lg) - 1)));
+        const int y = (int)(((tile / tiles_x) << th_lg) + (pl >> tw_lg));
         const bool valid = x < a.width && y < a.height;
         const int64_t pix = valid ? (int64_t)y * a.width + x : 0;
         Ray<N> r;
@@ -68,18 +76,21 @@ __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
         r.t_max = a.t_max;
         r.any_hit = false;
         float acc[3] = {0.0f, 0.0f, 0.0f};
-        for (int pass = 0; pass < a.spp; ++pass) {
+        const int n_rounds = (a.spp + L - 1) >> lg;
+        for (int j = 0; j < n_rounds; ++j) {
+            const int pass = (j << lg) + sub;
+            const bool live = valid && pass < a.spp;
 #pragma unroll
             for (int k = 0; k < N; ++k) r.slot[k] = Slot{INFINITY, INFINITY, 0.0f, 0xffffffffu};
             update_clip(r, a.t_max);
-            if (!valid) r.t_far = -INFINITY;  // lanes off the image never hit
+            if (!live) r.t_far = -INFINITY;  // lanes off the image never hit
             if (a.n_nodes > 0) {
                 if (FMT == GS_NODES_BINARY)
                     traverse_packet<N, COUNT>(a, r, pass, stack, stack_t, err, cnt);
                 else
                     traverse_packet_wide<N, COUNT, FMT>(a, r, pass, stack, stack_t, err, cnt);
             }
-            if (valid) {
+            if (live) {
                 // shade each slot once (Eq. 6) and accumulate (Eq. 7)
                 float Y[16];
                 sh_basis(a.sh_degree, r.d, Y);
@@ -104,7 +115,13 @@ __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
             }
             __syncwarp();
         }
-        if (valid) {
+        // the pixel's lanes add their partial sums (Eq. 7)
+        for (int o = L >> 1; o >= 1; o >>= 1) {
+            acc[0] += __shfl_xor_sync(kAll, acc[0], o);
+            acc[1] += __shfl_xor_sync(kAll, acc[1], o);
+            acc[2] += __shfl_xor_sync(kAll, acc[2], o);
+        }
+        if (valid && sub == 0) {
             const float inv_n = 1.0f / (float)((int64_t)a.spp * N);
             a.rgb[3 * pix + 0] = acc[0] * inv_n;
             a.rgb[3 * pix + 1] = acc[1] * inv_n;
@@ -134,7 +151,9 @@ gs_status launch_nf(const TraceArgs &a, bool count, cudaStream_t s) {
                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<N, false, FMT>, kThreads, 0);
     if (e != cudaSuccess) return cuda_fail(e, "trace launch setup");
     // one resident grid; warps take tiles until none is left
-    const uint32_t tiles = (uint32_t)(((a.width + 7) / 8) * ((a.height + 3) / 4));
+    const int tw_lg = tile_w_log2(a.lpp_log2), th_lg = 5 - a.lpp_log2 - tw_lg;
+    const uint32_t tiles = (uint32_t)(((a.width + (1 << tw_lg) - 1) >> tw_lg) *
+                                      ((a.height + (1 << th_lg) - 1) >> th_lg));
     const uint32_t warps_needed = tiles;
     uint32_t blocks = (uint32_t)sms * (uint32_t)(per > 0 ? per : 1);
     const uint32_t max_blocks = (warps_needed + kThreads / 32 - 1) / (kThreads / 32);
@@ -193,6 +212,7 @@ gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole 
     a.counters = p->counters;
     a.status = b->status;
     a.work = b->status + 1;
+    a.lpp_log2 = lanes_per_pixel_log2(p->spp);
     a.depth_mode = p->depth_mode;
     a.rng_mode = p->rng_mode;
     {

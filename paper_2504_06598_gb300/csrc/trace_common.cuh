@@ -40,6 +40,7 @@ struct TraceArgs {
     unsigned long long *counters;
     uint32_t *status;
     uint32_t *work;  // tile counter of the persistent launch
+    int lpp_log2;    // log2 of the lanes that trace samples of one pixel
     int depth_mode;  // 0: 1D mean; 1: centre projected on fwd (camera rays)
     int rng_mode;    // 0: Philox; 1: trigonometric hash of the hit point
     float fwd[3];    // camera forward axis (depth_mode 1)
@@ -49,6 +50,22 @@ struct TraceArgs {
     const float *quats;        // derivatives
     float *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh;
 };
+
+// A warp traces a tile of 32 >> lpp_log2 pixels, each pixel on 1 << lpp_log2
+// consecutive lanes that take interleaved samples of the same camera ray.
+// Tile width in pixels (a power of two); the height is the rest.
+__host__ __device__ __forceinline__ int tile_w_log2(int lpp_log2) {
+    const int px_log2 = 5 - lpp_log2;  // 32, 16, 8, 4, 2, 1 pixels
+    return px_log2 >= 4 ? px_log2 - 2 : (px_log2 >= 2 ? px_log2 - 1 : px_log2);
+}
+
+// Lanes per pixel for a launch of spp passes: the largest power of two not
+// above spp, at most the warp.
+inline int lanes_per_pixel_log2(int spp) {
+    int l = 0;
+    while (l < 5 && (2 << l) <= spp) ++l;
+    return l;
+}
 
 // ---------------------------------------------------------------- Philox
 // Philox-4x32-10 (Salmon et al., SC'11): ten rounds, multipliers

@@ -2,9 +2,12 @@
 // persistent launch (the path-tracing integration of Sec. 5: Gaussians
 // among other assets cast soft shadows and light their surroundings).
 //
-// Warps take 8x4 pixel tiles from one queue spanning every view (views of
-// uneven size balance through the queue). For each sample a warp traces,
-// as packets: the camera rays of its tile; for the lanes whose camera ray
+// Warps take pixel tiles from one queue spanning every view (views of
+// uneven size balance through the queue). As in the single-view trace, the
+// L lanes of a pixel (L the largest power of two not above spp, at most 32)
+// take interleaved samples of it, so an 8x4 tile at spp = 1 becomes one
+// pixel x 32 samples at spp >= 32. For each round of samples a warp traces,
+// as packets: the camera rays of its lanes; for the lanes whose camera ray
 // reaches the ground first, one shadow packet per light (any-hit: a lane
 // stops at its first accepted Gaussian) and one bounce packet (closest
 // accepted Gaussian). Each ray type has its own Philox stream tag, so the
@@ -96,6 +99,9 @@ __global__ void k_render_views(const WaveArgs w) {
     const TraceArgs &a = w.t;
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;
+    const int lg = a.lpp_log2, L = 1 << lg;
+    const int tw_lg = tile_w_log2(lg), th_lg = 5 - lg - tw_lg;
+    const int sub = lane & (L - 1), pl = lane >> lg;
     uint32_t stack[STACK];
     float stack_t[STACK];
     uint32_t err = 0;
@@ -110,8 +116,8 @@ __global__ void k_render_views(const WaveArgs w) {
         while (v + 1 < w.n_views && w.views[v + 1].tile_begin <= tile) ++v;
         const ViewDesc &vw = w.views[v];
         const uint32_t lt = tile - vw.tile_begin;
-        const int x = (int)((lt % vw.tiles_x) * 8 + (lane & 7));
-        const int y = (int)((lt / vw.tiles_x) * 4 + (lane >> 3));
+        const int x = (int)(((lt % vw.tiles_x) << tw_lg) + (pl & ((1 << tw_lg) - 1)));
+        const int y = (int)(((lt / vw.tiles_x) << th_lg) + (pl >> tw_lg));
         const bool valid = x < vw.width && y < vw.height;
         const int64_t lpix = valid ? (int64_t)y * vw.width + x : 0;
         const uint32_t ray_id = vw.ray_id_offset + (uint32_t)lpix;
@@ -133,7 +139,10 @@ __global__ void k_render_views(const WaveArgs w) {
         }
         // shadow directions and distances (fixed for the pixel)
         float acc[3] = {0.0f, 0.0f, 0.0f};
-        for (int s = 0; s < a.spp; ++s) {
+        const int n_rounds = (a.spp + L - 1) >> lg;
+        for (int j = 0; j < n_rounds; ++j) {
+            const int s = (j << lg) + sub;
+            const bool live = valid && s < a.spp;
             // camera ray
             Ray<1> r;
             set_ray(r, vw.eye, d0);
@@ -144,11 +153,11 @@ __global__ void k_render_views(const WaveArgs w) {
             r.any_hit = false;
             reset_slots(r);
             update_clip(r, r.t_max);
-            if (!valid) r.t_far = -INFINITY;
+            if (!live) r.t_far = -INFINITY;
             trace_packet<FMT, COUNT>(a, r, s, stack, stack_t, err, cnt);
-            n_cam += valid;
-            const bool gauss = valid && r.slot[0].gid != 0xffffffffu && r.slot[0].t < tq;
-            const bool on_ground = valid && ground && !gauss;
+            n_cam += live;
+            const bool gauss = live && r.slot[0].gid != 0xffffffffu && r.slot[0].t < tq;
+            const bool on_ground = live && ground && !gauss;
             float c[3] = {a.bg[0], a.bg[1], a.bg[2]};
             int32_t diag_cam = -1, diag_bounce = -1, diag_vis = 0;
             if (gauss) {
@@ -219,7 +228,7 @@ __global__ void k_render_views(const WaveArgs w) {
                     }
                 }
             }
-            if (valid) {
+            if (live) {
                 acc[0] += c[0];
                 acc[1] += c[1];
                 acc[2] += c[2];
@@ -232,7 +241,13 @@ __global__ void k_render_views(const WaveArgs w) {
             }
             __syncwarp();
         }
-        if (valid) {
+        // the pixel's lanes add their partial sums
+        for (int o = L >> 1; o >= 1; o >>= 1) {
+            acc[0] += __shfl_xor_sync(kAll, acc[0], o);
+            acc[1] += __shfl_xor_sync(kAll, acc[1], o);
+            acc[2] += __shfl_xor_sync(kAll, acc[2], o);
+        }
+        if (valid && sub == 0) {
             const float inv_n = 1.0f / (float)a.spp;
             const int64_t o = 3 * (vw.pix_begin + lpix);
             a.rgb[o] = acc[0] * inv_n;
@@ -305,6 +320,8 @@ gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_p
     a.rgb = rgb;
     a.status = b->status;
     a.work = b->status + 1;
+    a.lpp_log2 = lanes_per_pixel_log2(p->spp);
+    const int tw_lg = tile_w_log2(a.lpp_log2), th_lg = 5 - a.lpp_log2 - tw_lg;
     uint32_t tiles = 0;
     int64_t pix = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -318,10 +335,10 @@ gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_p
         d.width = cams[v].width;
         d.height = cams[v].height;
         d.ray_id_offset = cams[v].ray_id_offset;
-        d.tiles_x = (uint32_t)((cams[v].width + 7) / 8);
+        d.tiles_x = (uint32_t)((cams[v].width + (1 << tw_lg) - 1) >> tw_lg);
         d.tile_begin = tiles;
         d.pix_begin = pix;
-        tiles += d.tiles_x * (uint32_t)((cams[v].height + 3) / 4);
+        tiles += d.tiles_x * (uint32_t)((cams[v].height + (1 << th_lg) - 1) >> th_lg);
         pix += (int64_t)cams[v].width * cams[v].height;
     }
     w.n_views = n_views;

@@ -47,7 +47,7 @@ def _gpu_grads(gs, cloud, cam, d_rgb, **opts):
     return {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
 
 
-@pytest.mark.parametrize("spp,n_hits", [(4, 1), (2, 4), (3, 2)])
+@pytest.mark.parametrize("spp,n_hits", [(4, 1), (2, 4), (3, 2), (40, 1)])
 def test_estimator_parity(gs, spp, n_hits):
     cloud = _cluster()
     cam = scenes.Pinhole(width=16, height=12, fov_y_deg=9.0)

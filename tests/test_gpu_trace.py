@@ -60,7 +60,9 @@ def colour_ok(g, r, same):
     return True
 
 
-@pytest.mark.parametrize("spp,n_hits", [(1, 1), (16, 1), (4, 4), (2, 8), (3, 2)])
+# spp picks the lanes per pixel (largest power of two <= spp, at most 32):
+# 1, 16, 4, 2 and 2 lanes here; 5 and 40 end on a partial round of samples.
+@pytest.mark.parametrize("spp,n_hits", [(1, 1), (16, 1), (4, 4), (2, 8), (3, 2), (5, 1), (40, 1)])
 def test_tiny_parity(gs, spp, n_hits):
     cloud = scenes.tiny_cloud(0)
     cam = scenes.default_camera(64, 64)
@@ -72,6 +74,15 @@ def test_shell_small_ragged(gs):
     cloud = scenes.shell_cloud(1, M=20000)
     cam = scenes.default_camera(100, 61)
     _assert_parity(gs, cloud, cam, spp=4, n_hits=1, seed=5)
+
+
+def test_shell_ragged_whole_warp_per_pixel(gs):
+    """spp = 33: one pixel per warp, the second round has one live lane;
+    image size not a multiple of any tile; a seeded pixel subset."""
+    cloud = scenes.shell_cloud(4, M=20000)
+    cam = scenes.default_camera(100, 61)
+    pix = scenes.pixel_subset(100, 61, 300, seed=11)
+    _assert_parity(gs, cloud, cam, spp=33, n_hits=1, seed=6, pixels=pix)
 
 
 def test_passes_by_hits_invariance(gs):
