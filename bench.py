@@ -65,7 +65,8 @@ def run_wavefront(args):
     """Batched form: the 1M shell above a Lambertian ground quad, 16 views of
     resolution uniform between 256x256 and 1920x1080, four point lights and
     one diffuse bounce, 16 spp, N=1. The launch shape and node format come
-    from the autotuner (searched on a 1-spp copy of the workload); each frame
+    from the autotuner (searched on the same workload, one timed frame per
+    candidate); each frame
     (hierarchy rebuild + the persistent render) is replayed from a CUDA graph.
     The FP32 form and the reduced-precision form (FP16 SH, 8-bit 4-wide
     boxes) are timed side by side."""
@@ -89,7 +90,7 @@ def run_wavefront(args):
     for name, dt, formats in (("fp32", torch.float32, ("binary", "wide4")),
                               ("fp16-q8", torch.float16, ("wide4_q8",))):
         g = gs.Gaussians.from_cloud(cloud, sh_dtype=dt)
-        tune = autotune.autotune(g, cams, ex, spp=1, repeats=1, formats=formats)
+        tune = autotune.autotune(g, cams, ex, spp=spp, repeats=1, formats=formats)
         bvh = gs.build_bvh(g, node_format=tune["node_format"])
         cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
         gs.render_views(bvh, g, cams, ex, seed=0, spp=spp, counters=cnt,
@@ -479,12 +480,15 @@ def main():
     sh_bytes = 16 * 3 * 4
 
     def roof(v, trace_ms, n_hits):
-        # per-ray algorithmic bytes: each ray's own node entries and Gaussian
+        # spp >= 8 on binary nodes runs the grouped 8-wide traversal, whose
+        # counters count 32-byte child records instead of 64-byte nodes
+        rec = 32 if (info["node_format"] == 0 and v["spp"] >= 8) else info["node_bytes"]
+        # per-ray algorithmic bytes: each ray's own node records and Gaussian
         # tests, one SH record per shaded sample, the pixel's output
-        alg = (info["node_bytes"] * v["nodes"] + info["prim_bytes"] * v["prims"]
+        alg = (rec * v["nodes"] + info["prim_bytes"] * v["prims"]
                + sh_bytes * v["shaded"] + 12 * npix)
-        # bytes the warps actually request (a node or record once per warp)
-        warp = (info["node_bytes"] * v["node_fetch"] + info["prim_bytes"] * v["prim_fetch"]
+        # bytes the warps (groups) actually request: a record once per fetch
+        warp = (rec * v["node_fetch"] + info["prim_bytes"] * v["prim_fetch"]
                 + sh_bytes * v["shaded"] + 12 * npix)
         ach = alg / (trace_ms * 1e-3) / 1e9
         traffic = recorded_traffic(n_hits)
@@ -492,7 +496,8 @@ def main():
                "frac": ach / peak, "traffic": traffic,
                "alg_bytes_per_launch": alg, "warp_request_bytes_per_launch": warp,
                "warp_request_gbs": warp / (trace_ms * 1e-3) / 1e9,
-               "peak_kind": peak_kind, "kernel": "k_trace<%d>" % n_hits}
+               "peak_kind": peak_kind, "kernel": "k_trace<%d>" % n_hits,
+               "node_record_bytes": rec}
         if traffic is not None:
             # what DRAM actually moved (ncu counters) over this run's duration
             out["dram_gbs"] = traffic / (trace_ms * 1e-3) / 1e9
@@ -512,16 +517,16 @@ def main():
         "roofline": roof(visits[1], r1["trace_ms"], 1),
         "build_ms": r1["build_ms"], "trace_ms": r1["trace_ms"],
         "trace_mrays_per_s": npix * SPP_N1 / (r1["trace_ms"] * 1e-3) / 1e6,
-        "visits_per_ray": {"nodes": visits[1]["nodes"] / visits[1]["rays"] / SPP_N1,
+        "visits_per_ray": {"node_records": visits[1]["nodes"] / visits[1]["rays"] / SPP_N1,
                            "prims": visits[1]["prims"] / visits[1]["rays"] / SPP_N1,
                            "philox": visits[1]["philox"] / visits[1]["rays"] / SPP_N1,
-                           "warp_node_fetches_per_ray": visits[1]["node_fetch"] / visits[1]["rays"] / SPP_N1},
+                           "fetched_node_records_per_ray": visits[1]["node_fetch"] / visits[1]["rays"] / SPP_N1},
         "n4": {"spp": SPP_N4, "samples_per_pixel": SPP_N4 * 4, "ms_per_step": r4["step_ms"],
                "trace_ms": r4["trace_ms"],
                "mrays_per_s": npix * SPP_N4 * world / (r4["step_ms"] * 1e-3) / 1e6,
                "msamples_per_s": npix * SPP_N4 * 4 * world / (r4["step_ms"] * 1e-3) / 1e6,
                "roofline": roof(visits[4], r4["trace_ms"], 4),
-               "visits_per_ray": {"nodes": visits[4]["nodes"] / visits[4]["rays"] / SPP_N4,
+               "visits_per_ray": {"node_records": visits[4]["nodes"] / visits[4]["rays"] / SPP_N4,
                                   "prims": visits[4]["prims"] / visits[4]["rays"] / SPP_N4},
                "clocks": r4["clocks"]},
         "msamples_per_s_n1": value,

@@ -111,7 +111,9 @@ typedef struct gs_pinhole {
  *                    axis (Sec. 4.1); alpha stays the 1D peak
  *                    (gs_trace_stochastic only; this depth is not a ray
  *                    parameter, so accepted hits do not clip the traversal)
- *   stack_depth   traversal stack entries per ray, 1..96 (0 = 96)
+ *   stack_depth   traversal stack entries per ray, 1..96 (0 = 96), for
+ *                 the per-lane stacks; the grouped traversal (see
+ *                 gs_trace_stochastic) keeps 128 entries per group instead
  *   stream_tag    fourth Philox counter word, separates ray streams
  *   rng_mode      0: keyed Philox (above); 1: the trigonometric hash of
  *                 the hit point of Eq. 8-9, moved per sample by
@@ -123,7 +125,10 @@ typedef struct gs_pinhole {
  *                 tested (Alg. 1 runs), Philox calls, rays (pixels),
  *                 samples shaded with a Gaussian's colour, node records
  *                 fetched by warps, Gaussian records fetched by warps};
- *                 NULL disables counting (the default fast path). */
+ *                 in the grouped traversal the first and the sixth count
+ *                 32-byte child records (of the 8-wide nodes each ray
+ *                 enters, and that each group fetches); NULL disables
+ *                 counting (the default fast path). */
 typedef struct gs_trace_params {
     uint64_t seed;
     int32_t spp;
@@ -144,7 +149,10 @@ typedef struct gs_trace_params {
 typedef struct gs_bvh gs_bvh;
 
 /* Node format the traversal reads (the binary tree is always built too).
- *   GS_NODES_BINARY    64-byte binary nodes, FP32 child boxes
+ *   GS_NODES_BINARY    64-byte binary nodes, FP32 child boxes; the handle
+ *                      also holds an 8-wide copy (one 32-byte FP32 record
+ *                      per child, M + (M - 1) records at most) for the
+ *                      grouped traversal, unless M > 2^27
  *   GS_NODES_WIDE4     128-byte 4-wide nodes, FP32 child boxes
  *   GS_NODES_WIDE4_Q8  64-byte 4-wide nodes, child boxes quantised to 8 bits
  *                      per plane with outward rounding (a decoded box always
@@ -235,6 +243,13 @@ gs_status gs_bvh_export_wide(const gs_bvh *bvh, void *out, int64_t capacity, int
  *   hit_t_out  device float[spp][n_hits][height][width] depth of each
  *              sample's hit (ray parameter, d is unit length) or +inf;
  *              NULL to skip
+ * The 32 lanes of a warp split into pixels x samples: the L lanes of a pixel
+ * (L the largest power of two not above spp, at most 32) trace passes
+ * j*L + lane of the same ray. With L >= 8 and a GS_NODES_BINARY handle a
+ * group of L lanes traverses the 8-wide copy together (each lane tests one
+ * child box, evaluates one hit Gaussian's depth and alpha, and draws for its
+ * own samples); otherwise each lane traverses the nodes of the handle's
+ * format in a warp packet. Every form returns the same hits.
  * Deterministic: identical inputs give bit-identical outputs. Traces that use
  * the same handle share its tile counter and status word, so they must not
  * overlap on the GPU: issue them on one stream (or order their streams). */

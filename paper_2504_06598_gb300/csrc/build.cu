@@ -549,6 +549,84 @@ __global__ void k_collapse(int64_t n_int, const Node *__restrict__ nodes,
     }
 }
 
+// The 8-wide hierarchy: one wide node per binary internal node at depth
+// 0 mod 3, whose children are its descendants three levels down, or the
+// leaves met before. Expands node i into up to 8 (reference, box) entries.
+__device__ __forceinline__ int expand8(const Node *__restrict__ nodes, uint32_t i, uint32_t ref[8],
+                                       float box[8][6]) {
+    int n = 0;
+    const Node nd = nodes[i];
+    for (int sd = 0; sd < 2; ++sd) {
+        ref[n] = nd.child[sd];
+        for (int q = 0; q < 6; ++q) box[n][q] = nd.box[sd][q];
+        ++n;
+    }
+    for (int level = 1; level < 3; ++level) {
+        // expand in place from the back so entries keep left-to-right order
+        int m = n;
+        for (int j = 0; j < n; ++j)
+            if (!(ref[j] & kLeafBit)) ++m;
+        for (int j = n - 1, dst = m - 1; j >= 0; --j) {
+            if (ref[j] & kLeafBit) {
+                ref[dst] = ref[j];
+                for (int q = 0; q < 6; ++q) box[dst][q] = box[j][q];
+                --dst;
+            } else {
+                const Node cn = nodes[ref[j]];
+                for (int sd = 1; sd >= 0; --sd) {
+                    ref[dst] = cn.child[sd];
+                    for (int q = 0; q < 6; ++q) box[dst][q] = cn.box[sd][q];
+                    --dst;
+                }
+            }
+        }
+        n = m;
+    }
+    return n;
+}
+
+// Children of the wide node at each binary internal node (0 where none);
+// the same count seeds the offsets.
+__global__ void k_count8(int64_t n_int, const Node *__restrict__ nodes,
+                         const uint32_t *__restrict__ parent_int, uint32_t *__restrict__ cnt,
+                         uint32_t *__restrict__ off) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    uint32_t d = 0, p = (uint32_t)i;
+    while (p != 0 && d < 4096) {
+        p = parent_int[p];
+        ++d;
+    }
+    uint32_t c = 0;
+    if (d % 3u == 0u) {
+        uint32_t ref[8];
+        float box[8][6];
+        c = (uint32_t)expand8(nodes, (uint32_t)i, ref, box);
+    }
+    cnt[i] = c;
+    off[i] = c;
+}
+
+// Writes the child records of every wide node at its offset.
+__global__ void k_collapse8(int64_t n_int, const Node *__restrict__ nodes,
+                            const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ off,
+                            Child8 *__restrict__ rec) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int || cnt[i] == 0u) return;
+    uint32_t ref[8];
+    float box[8][6];
+    const int n = expand8(nodes, (uint32_t)i, ref, box);
+    Child8 *dst = rec + off[i];
+    for (int j = 0; j < n; ++j) {
+        Child8 c;
+        for (int q = 0; q < 3; ++q) { c.lo[q] = box[j][q]; c.hi[q] = box[j][3 + q]; }
+        const uint32_t r = ref[j];
+        c.child = (r & kLeafBit) ? r : (((cnt[r] - 1u) << kW8CountShift) | off[r]);
+        c.reserved = 0;
+        dst[j] = c;
+    }
+}
+
 inline unsigned grid_for(int64_t n, int threads) {
     return (unsigned)((n + threads - 1) / threads);
 }
@@ -614,6 +692,13 @@ gs_status build_into(gs_bvh *b, const gs_gaussians *g, cudaStream_t s) {
         else
             k_collapse<GS_NODES_WIDE4_Q8><<<grid_for(n_int, 256), 256, 0, s>>>(
                 n_int, b->nodes, b->depth, b->wmap, b->wide);
+    }
+    if (b->wide8) {
+        const int64_t n_int = b->n_nodes;
+        k_count8<<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->nodes, b->parent, b->cnt8, b->off8);
+        scan_exclusive(b->off8, n_int, b->scan_tmp, s);
+        k_collapse8<<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->nodes, b->cnt8, b->off8,
+                                                         b->wide8);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "build launch");
     return GS_OK;

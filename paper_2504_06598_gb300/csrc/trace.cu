@@ -36,11 +36,17 @@
 namespace gsrt {
 namespace {
 
+// Template value of FMT for the cooperative traversal of the 8-wide records
+// (groups of 8 or more lanes on one pixel); the others are GS_NODES_*.
+constexpr int kFmtCoop8 = 8;
+
 // Persistent kernel: each warp repeatedly takes the next tile (one atomic
 // per tile, so the tail of the launch stays balanced), then runs all passes
-// of its pixels.
+// of its pixels. The cooperative form is latency-bound and is built for
+// eight resident blocks per SM (five with eight slots per lane).
 template <int N, bool COUNT, int FMT>
-__global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
+__global__ void __launch_bounds__(kThreads, FMT == kFmtCoop8 ? (N >= 8 ? 5 : kCoopMinBlocks) : 1)
+    k_trace(const TraceArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;
     const int lg = a.lpp_log2, L = 1 << lg;
@@ -55,6 +61,12 @@ __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
     uint32_t err = 0;
     Counts cnt;
     unsigned long long n_shaded = 0, n_rays = 0;
+    constexpr bool coop = FMT == kFmtCoop8;
+    __shared__ uint32_t s_ref[coop ? kThreads / 32 : 1][kCoopGroupsPerWarp][coop ? kCoopStack : 1];
+    __shared__ float s_t[coop ? kThreads / 32 : 1][kCoopGroupsPerWarp][coop ? kCoopStack : 1];
+    const int grp = coop ? (lane >> lg) : 0;
+    uint32_t *grp_ref = s_ref[coop ? threadIdx.x >> 5 : 0][grp];
+    float *grp_t = s_t[coop ? threadIdx.x >> 5 : 0][grp];
     for (;;) {
         uint32_t tile = 0;
         if (lane == 0) tile = atomicAdd(a.work, 1u);
@@ -85,7 +97,9 @@ __global__ void __launch_bounds__(kThreads) k_trace(const TraceArgs a) {
             update_clip(r, a.t_max);
             if (!live) r.t_far = -INFINITY;  // lanes off the image never hit
             if (a.n_nodes > 0) {
-                if (FMT == GS_NODES_BINARY)
+                if constexpr (coop)
+                    traverse_coop8<N, COUNT>(a, r, pass, lg, grp_ref, grp_t, err, cnt);
+                else if constexpr (FMT == GS_NODES_BINARY)
                     traverse_packet<N, COUNT>(a, r, pass, stack, stack_t, err, cnt);
                 else
                     traverse_packet_wide<N, COUNT, FMT>(a, r, pass, stack, stack_t, err, cnt);
@@ -167,6 +181,9 @@ gs_status launch_nf(const TraceArgs &a, bool count, cudaStream_t s) {
 
 template <int N>
 gs_status launch_n(const TraceArgs &a, int format, bool count, cudaStream_t s) {
+    // groups of 8 or more lanes on one pixel take the cooperative form
+    if (format == GS_NODES_BINARY && a.wide8 != nullptr && a.lpp_log2 >= 3)
+        return launch_nf<N, kFmtCoop8>(a, count, s);
     switch (format) {
         case GS_NODES_WIDE4: return launch_nf<N, GS_NODES_WIDE4>(a, count, s);
         case GS_NODES_WIDE4_Q8: return launch_nf<N, GS_NODES_WIDE4_Q8>(a, count, s);
@@ -182,6 +199,8 @@ gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole 
     TraceArgs a;
     a.nodes = b->nodes;
     a.wide = b->wide;
+    a.wide8 = b->wide8;
+    a.cnt8 = b->cnt8;
     a.prims = b->prims;
     a.sh = g->sh;
     a.n_nodes = b->n_nodes;

@@ -19,6 +19,8 @@ constexpr int kThreads = 128;
 struct TraceArgs {
     const Node *nodes;
     const void *wide;  // Node4 or NodeQ4 when the handle has wide nodes
+    const Child8 *wide8;   // 8-wide child records (binary format), or null
+    const uint32_t *cnt8;  // their per-node child counts (root at 0)
     const PrimRec *prims;
     const void *sh;
     int64_t n_nodes;
@@ -279,15 +281,32 @@ __device__ __forceinline__ float hash_xi(const float p[3], uint32_t s) {
     return fract_f(43758.5453f * sinf(12.9898f * (q[0] + r1) + 78.233f * (q[1] + r1)));
 }
 
-// Alg. 1 for primitive record idx against all N slots of the current pass.
-template <int N, bool COUNT>
-__device__ __forceinline__ void intersect(const TraceArgs &a, Ray<N> &r, uint32_t idx, int pass,
-                                          unsigned long long &n_draws) {
+// Alg. 1, split in three so that the cooperative traversal can evaluate
+// the sample-independent part once per Gaussian and ray:
+//   cand_depth  the record, the base point and the 1D mean (its depth key),
+//               and the range test t_min < t < t_max;
+//   cand_alpha  the refined minimum q, the ellipsoid test q <= s^2 and alpha;
+//   accept      the draws of this lane's samples that are closer than their
+//               slots, replacing slots and clipping.
+struct CandGeom {
+    float m[9];
+    float w[3], md[3];
+    float inv_dd, tau;
+    float t, key_tc, key_tau;
+    float opacity;
+    uint32_t gid;
+};
+
+template <int N>
+__device__ __forceinline__ bool cand_depth(const TraceArgs &a, const Ray<N> &r, uint32_t idx,
+                                           CandGeom &c) {
     const float4 *pp = reinterpret_cast<const float4 *>(a.prims + idx);
     const float4 p0 = __ldg(pp), p1 = __ldg(pp + 1), p2 = __ldg(pp + 2), p3 = __ldg(pp + 3);
     const float mu[3] = {p0.x, p0.y, p0.z};
-    const float m[9] = {p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w, p3.x};
-    const uint32_t gid = __float_as_uint(p3.y);
+    c.m[0] = p1.x; c.m[1] = p1.y; c.m[2] = p1.z; c.m[3] = p1.w;
+    c.m[4] = p2.x; c.m[5] = p2.y; c.m[6] = p2.z; c.m[7] = p2.w; c.m[8] = p3.x;
+    c.opacity = p0.w;
+    c.gid = __float_as_uint(p3.y);
     // o - mu = h + l exactly (two-sum)
     float h[3], l[3];
 #pragma unroll
@@ -299,51 +318,55 @@ __device__ __forceinline__ void intersect(const TraceArgs &a, Ray<N> &r, uint32_
         h[i] = s;
     }
     const float tc = -fmaf(h[0], r.d[0], fmaf(h[1], r.d[1], h[2] * r.d[2]));
-    float w[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) w[i] = fmaf(tc, r.d[i], h[i]) + l[i];
-    float md[3], mw[3];
+    for (int i = 0; i < 3; ++i) c.w[i] = fmaf(tc, r.d[i], h[i]) + l[i];
+    float mw[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        md[i] = fmaf(m[3 * i], r.d[0], fmaf(m[3 * i + 1], r.d[1], m[3 * i + 2] * r.d[2]));
-        mw[i] = fmaf(m[3 * i], w[0], fmaf(m[3 * i + 1], w[1], m[3 * i + 2] * w[2]));
+        c.md[i] = fmaf(c.m[3 * i], r.d[0], fmaf(c.m[3 * i + 1], r.d[1], c.m[3 * i + 2] * r.d[2]));
+        mw[i] = fmaf(c.m[3 * i], c.w[0], fmaf(c.m[3 * i + 1], c.w[1], c.m[3 * i + 2] * c.w[2]));
     }
-    const float dd = fmaf(md[0], md[0], fmaf(md[1], md[1], md[2] * md[2]));
-    const float wd = fmaf(mw[0], md[0], fmaf(mw[1], md[1], mw[2] * md[2]));
-    const float inv_dd = 1.0f / dd;
-    const float tau = -wd * inv_dd;
-    float t = tc + tau;
+    const float dd = fmaf(c.md[0], c.md[0], fmaf(c.md[1], c.md[1], c.md[2] * c.md[2]));
+    const float wd = fmaf(mw[0], c.md[0], fmaf(mw[1], c.md[1], mw[2] * c.md[2]));
+    c.inv_dd = 1.0f / dd;
+    c.tau = -wd * c.inv_dd;
+    c.t = tc + c.tau;
     // depth key (tc, tau); the projected-centre depth uses (centre, 0)
-    float key_tc = tc, key_tau = tau;
+    c.key_tc = tc;
+    c.key_tau = c.tau;
     if (a.depth_mode == 1) {
         const float hf = fmaf(h[0], a.fwd[0], fmaf(h[1], a.fwd[1], h[2] * a.fwd[2]));
         const float lf = fmaf(l[0], a.fwd[0], fmaf(l[1], a.fwd[1], l[2] * a.fwd[2]));
-        t = -(hf + lf);
-        key_tc = t;
-        key_tau = 0.0f;
+        c.t = -(hf + lf);
+        c.key_tc = c.t;
+        c.key_tau = 0.0f;
     }
-    // Alg. 1 range test; t_far only prunes hits behind every slot
-    if (!(t > r.t_min) || !(t < r.t_max) || !(t <= r.t_far)) return;
-    bool closer[N];
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        closer[k] = lex_closer(key_tc, key_tau, gid, r.slot[k]);
-        any |= closer[k];
-    }
-    if (!any) return;
-    // refine the base point to the 1D mean, then the ellipsoid test (Eq. 2)
+    return (c.t > r.t_min) && (c.t < r.t_max);
+}
+
+// Refine the base point to the 1D mean, then the ellipsoid test (Eq. 2).
+template <int N>
+__device__ __forceinline__ bool cand_alpha(const Ray<N> &r, const CandGeom &c, float &alpha) {
     float w2[3], mw2[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) w2[i] = fmaf(tau, r.d[i], w[i]);
+    for (int i = 0; i < 3; ++i) w2[i] = fmaf(c.tau, r.d[i], c.w[i]);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-        mw2[i] = fmaf(m[3 * i], w2[0], fmaf(m[3 * i + 1], w2[1], m[3 * i + 2] * w2[2]));
+        mw2[i] = fmaf(c.m[3 * i], w2[0], fmaf(c.m[3 * i + 1], w2[1], c.m[3 * i + 2] * w2[2]));
     const float ww = fmaf(mw2[0], mw2[0], fmaf(mw2[1], mw2[1], mw2[2] * mw2[2]));
-    const float wd2 = fmaf(mw2[0], md[0], fmaf(mw2[1], md[1], mw2[2] * md[2]));
-    const float q = fmaxf(ww - wd2 * wd2 * inv_dd, 0.0f);
-    if (!(q <= kS2)) return;
-    const float alpha = p0.w * expf(-0.5f * q);
+    const float wd2 = fmaf(mw2[0], c.md[0], fmaf(mw2[1], c.md[1], mw2[2] * c.md[2]));
+    const float q = fmaxf(ww - wd2 * wd2 * c.inv_dd, 0.0f);
+    if (!(q <= kS2)) return false;
+    alpha = c.opacity * expf(-0.5f * q);
+    return true;
+}
+
+// Eq. 4 for the slots that the candidate is closer than: accept iff
+// xi < alpha, replacing the slot (Eq. 6) and clipping the traversal range.
+template <int N, bool COUNT>
+__device__ __forceinline__ void accept(const TraceArgs &a, Ray<N> &r, int pass, const bool closer[N],
+                                       float t, float key_tc, float key_tau, float alpha,
+                                       uint32_t gid, unsigned long long &n_draws) {
     const uint32_t s0 = (uint32_t)pass * N;
     if (a.rng_mode == 1) {
         float ph[3];
@@ -363,7 +386,7 @@ __device__ __forceinline__ void intersect(const TraceArgs &a, Ray<N> &r, uint32_
         if (a.depth_mode == 1) r.t_far = r.t_max;
         return;
     }
-    // Eq. 4: one Philox call serves four consecutive samples
+    // one Philox call serves four consecutive samples
     uint4 u0 = make_uint4(0, 0, 0, 0), u1 = make_uint4(0, 0, 0, 0);
     u0 = philox10(make_uint4(r.ray_id, gid, s0 >> 2, r.stream_tag), a.key0, a.key1);
     if (N == 8) u1 = philox10(make_uint4(r.ray_id, gid, (s0 >> 2) + 1, r.stream_tag), a.key0, a.key1);
@@ -385,6 +408,34 @@ __device__ __forceinline__ void intersect(const TraceArgs &a, Ray<N> &r, uint32_
     // A projected-centre depth is not a ray parameter, so it cannot clip the
     // box tests: every box on the ray stays open and order is decided here.
     if (a.depth_mode == 1) r.t_far = r.t_max;
+}
+
+// Which slots a candidate at depth key (key_tc, key_tau) is closer than,
+// after the clip test t <= t_far (t_far only prunes hits behind every slot).
+template <int N>
+__device__ __forceinline__ bool closer_slots(const Ray<N> &r, float t, float key_tc, float key_tau,
+                                             uint32_t gid, bool closer[N]) {
+    if (!(t <= r.t_far)) return false;
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        closer[k] = lex_closer(key_tc, key_tau, gid, r.slot[k]);
+        any |= closer[k];
+    }
+    return any;
+}
+
+// Alg. 1 for primitive record idx against all N slots of the current pass.
+template <int N, bool COUNT>
+__device__ __forceinline__ void intersect(const TraceArgs &a, Ray<N> &r, uint32_t idx, int pass,
+                                          unsigned long long &n_draws) {
+    CandGeom c;
+    if (!cand_depth<N>(a, r, idx, c)) return;
+    bool closer[N];
+    if (!closer_slots<N>(r, c.t, c.key_tc, c.key_tau, c.gid, closer)) return;
+    float alpha;
+    if (!cand_alpha<N>(r, c, alpha)) return;
+    accept<N, COUNT>(a, r, pass, closer, c.t, c.key_tc, c.key_tau, alpha, c.gid, n_draws);
 }
 
 // Slab test of one child box against [t_min, t_far].
@@ -654,6 +705,141 @@ __device__ __forceinline__ void traverse_packet_wide(const TraceArgs &a, Ray<N> 
             if (__any_sync(kAll, want)) {
                 node = stack[sp];
                 active = want;
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+    }
+}
+
+
+// ---------------------------------------------------------------- groups
+constexpr int kCoopStack = 128;       // stack entries per group of lanes
+constexpr int kCoopGroupsPerWarp = 4; // groups of 8 or more lanes
+constexpr int kCoopMinBlocks = 8;     // resident blocks per SM to build for
+
+// Cooperative traversal of the 8-wide hierarchy by a group of L = 2^lg >= 8
+// lanes that trace different samples of one ray. The group visits a wide
+// node in one step: lane k tests child k against the group's clip (the
+// farthest of its lanes' clips). Lanes holding a hit leaf evaluate the
+// sample-independent part of Alg. 1 for it (cand_depth, cand_alpha); every
+// lane then draws for its own samples against each candidate (accept). The
+// nearest hit inner child is visited next and the other hit inner children
+// go to the group's stack in shared memory. Every node and leaf a lane's
+// own ray needs is visited, and each lane keeps its own slots and clip, so
+// per-lane results are those of an independent traversal.
+template <int N, bool COUNT>
+__device__ __forceinline__ void traverse_coop8(const TraceArgs &a, Ray<N> &r, int pass, int lg,
+                                               uint32_t *s_ref, float *s_t, uint32_t &err,
+                                               Counts &cnt) {
+    const int lane = threadIdx.x & 31;
+    const int L = 1 << lg;
+    const int base = lane & ~(L - 1);
+    const int sub = lane & (L - 1);
+    const uint32_t gmask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << base);
+    float G = r.t_far >= r.t_min ? r.t_far : -INFINITY;
+    for (int o = 1; o < L; o <<= 1) G = fmaxf(G, __shfl_xor_sync(gmask, G, o));
+    if (!(G >= r.t_min)) return;  // no lane of the group is live
+    int sp = 0;
+    uint32_t node = (__ldg(a.cnt8) - 1u) << kW8CountShift;  // the root's records start at 0
+    uint32_t steps = 0;
+    float node_t = r.t_min;
+    for (;;) {
+        if (++steps > a.step_limit) {
+            err |= kErrSteps;
+            break;
+        }
+        const int n_child = (int)(node >> kW8CountShift) + 1;
+        if (COUNT) {
+            // the child records of a wide node this lane's own ray enters
+            cnt.nodes += node_t <= r.t_far ? n_child : 0;
+            cnt.node_fetch += lane == base ? n_child : 0;
+        }
+        uint32_t ref = kEmpty;
+        float te = INFINITY;
+        bool hit = false;
+        if (sub < n_child) {
+            const float4 *cp =
+                reinterpret_cast<const float4 *>(a.wide8 + (node & kW8OffsetMask) + sub);
+            const float4 q0 = __ldg(cp), q1 = __ldg(cp + 1);
+            const float bx[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
+            ref = __float_as_uint(q1.z);
+            hit = slab(bx, r.inv, r.oinv, r.t_min, G, te);
+        }
+        const bool leaf = (ref & kLeafBit) != 0u;
+        const unsigned lm = (__ballot_sync(gmask, hit && leaf) >> base) & 0xffu;
+        if (lm) {
+            if (COUNT) {
+                for (unsigned m2 = lm; m2; m2 &= m2 - 1u) {
+                    const float tl = __shfl_sync(gmask, te, base + __ffs(m2) - 1);
+                    cnt.prims += tl <= r.t_far;
+                    cnt.prim_fetch += lane == base;
+                }
+            }
+            // one lane per hit leaf: the part of Alg. 1 all samples share
+            float ct = 0.0f, ck1 = 0.0f, ck2 = 0.0f, cal = 0.0f;
+            uint32_t cgid = 0;
+            bool ok = false;
+            if (hit && leaf) {
+                CandGeom c;
+                ok = cand_depth<N>(a, r, ref & ~kLeafBit, c) && cand_alpha<N>(r, c, cal);
+                ct = c.t;
+                ck1 = c.key_tc;
+                ck2 = c.key_tau;
+                cgid = c.gid;
+            }
+            // every lane: its own draws against each candidate
+            for (unsigned cm = (__ballot_sync(gmask, ok) >> base) & 0xffu; cm; cm &= cm - 1u) {
+                const int src = base + __ffs(cm) - 1;
+                const float t = __shfl_sync(gmask, ct, src);
+                const float key_tc = __shfl_sync(gmask, ck1, src);
+                const float key_tau = __shfl_sync(gmask, ck2, src);
+                const float alpha = __shfl_sync(gmask, cal, src);
+                const uint32_t gid = __shfl_sync(gmask, cgid, src);
+                bool closer[N];
+                if (closer_slots<N>(r, t, key_tc, key_tau, gid, closer))
+                    accept<N, COUNT>(a, r, pass, closer, t, key_tc, key_tau, alpha, gid, cnt.draws);
+            }
+            G = r.t_far >= r.t_min ? r.t_far : -INFINITY;
+            for (int o = 1; o < L; o <<= 1) G = fmaxf(G, __shfl_xor_sync(gmask, G, o));
+        }
+        const bool inner = hit && !leaf && te <= G;
+        const unsigned im = (__ballot_sync(gmask, inner) >> base) & 0xffu;
+        if (im) {
+            // nearest inner child next (ties and the low three mantissa
+            // bits of the entry distance broken by child index)
+            const uint32_t key = __reduce_min_sync(
+                gmask, inner ? ((__float_as_uint(fmaxf(te, 0.0f)) & ~7u) | (uint32_t)sub)
+                             : 0xffffffffu);
+            const int nj = (int)(key & 7u);
+            const uint32_t next = __shfl_sync(gmask, ref, base + nj);
+            const float next_t = __shfl_sync(gmask, te, base + nj);
+            const unsigned others = im & ~(1u << nj);
+            const int npush = __popc(others);
+            if (sp + npush > kCoopStack) {
+                err |= kErrStack;
+                break;
+            }
+            __syncwarp(gmask);  // earlier reads of these entries are done
+            if (inner && sub != nj) {
+                const int pos = sp + __popc(others & ((1u << sub) - 1u));
+                s_ref[pos] = ref;
+                s_t[pos] = te;
+            }
+            sp += npush;
+            __syncwarp(gmask);
+            node = next;
+            node_t = next_t;
+            continue;
+        }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            const float tt = s_t[sp];
+            if (tt <= G) {
+                node = s_ref[sp];
+                node_t = tt;
                 found = true;
                 break;
             }

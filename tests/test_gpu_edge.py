@@ -48,10 +48,11 @@ def _parity_ok(cloud, cam, seed, ids, rgb, spp, n_hits, pixels=None, bg=(0, 0, 0
     return agree, classes
 
 
-def test_empty_scene_is_background(gs):
+@pytest.mark.parametrize("spp", [2, 8])
+def test_empty_scene_is_background(gs, spp):
     cloud = scenes.tiny_cloud(0, M=0)
     cam = scenes.default_camera(20, 12)
-    rgb, ids, ts = _trace(gs, cloud, cam, spp=2, bg=(0.25, 0.5, 1.0))
+    rgb, ids, ts = _trace(gs, cloud, cam, spp=spp, bg=(0.25, 0.5, 1.0))
     assert np.all(rgb == np.array([0.25, 0.5, 1.0], np.float32))
     assert np.all(ids == -1) and np.all(np.isinf(ts))
 
@@ -66,13 +67,16 @@ def test_single_gaussian(gs):
     _parity_ok(cloud, cam, 3, ids, rgb, 8, 1)
 
 
-def test_coincident_means(gs):
+@pytest.mark.parametrize("spp", [4, 16])
+def test_coincident_means(gs, spp):
+    """All means equal: the key sort ties everywhere; spp=16 runs the
+    grouped 8-wide traversal on that tree."""
     cloud = scenes.tiny_cloud(5, M=500)
     cloud.means[:] = 0.01
     cloud.log_scales[:] += 1.5
     cam = scenes.default_camera(24, 24)
-    rgb, ids, _ = _trace(gs, cloud, cam, spp=4, seed=2)
-    _parity_ok(cloud, cam, 2, ids, rgb, 4, 1)
+    rgb, ids, _ = _trace(gs, cloud, cam, spp=spp, seed=2)
+    _parity_ok(cloud, cam, 2, ids, rgb, spp, 1)
 
 
 def test_nonfinite_parameters_reported(gs):
@@ -117,41 +121,50 @@ def test_stack_overflow_is_reported_then_cleared(gs):
     b = gs.trace_stochastic(bvh, g, cam, spp=2, stack_depth=48).cpu()
     bvh.sync_status()
     assert torch.equal(a, b)
+    # the grouped traversal (spp >= 8) keeps its own 128-entry group stacks
+    c = gs.trace_stochastic(bvh, g, cam, spp=8, stack_depth=1).cpu()
+    bvh.sync_status()
+    d = gs.trace_stochastic(bvh, g, cam, spp=8, stack_depth=0).cpu()
+    bvh.sync_status()
+    assert torch.equal(c, d)
     bvh.free()
 
 
-def test_counters_do_not_change_results(gs):
+@pytest.mark.parametrize("spp,n_hits", [(3, 4), (16, 1), (8, 8)])
+def test_counters_do_not_change_results(gs, spp, n_hits):
     cloud = scenes.shell_cloud(10, M=20000)
     cam = scenes.default_camera(64, 48)
     g = gs.Gaussians.from_cloud(cloud)
     bvh = gs.build_bvh(g)
     cnt = torch.zeros(7, dtype=torch.int64, device="cuda")
-    a = gs.trace_stochastic(bvh, g, cam, spp=3, n_hits=4, counters=cnt).cpu()
-    b = gs.trace_stochastic(bvh, g, cam, spp=3, n_hits=4).cpu()
+    a = gs.trace_stochastic(bvh, g, cam, spp=spp, n_hits=n_hits, counters=cnt).cpu()
+    b = gs.trace_stochastic(bvh, g, cam, spp=spp, n_hits=n_hits).cpu()
     bvh.sync_status()
     c = cnt.cpu().numpy()
     assert torch.equal(a, b)
     assert c[3] == 64 * 48 and c[0] > c[3] and c[1] > 0 and c[2] > 0 and c[4] > 0
-    # a warp fetches each node once for its 32 rays: fewer fetches than entries
+    # a warp (or group) fetches each node once for its rays: fewer fetches than entries
     assert 0 < c[5] < c[0] and 0 < c[6] <= c[1]
     bvh.free()
 
 
-def test_background_and_ray_offset(gs):
+@pytest.mark.parametrize("spp", [4, 8])
+def test_background_and_ray_offset(gs, spp):
     cloud = scenes.tiny_cloud(11)
     cam = scenes.Pinhole(width=40, height=30, ray_id_offset=123456, eye=(0.5, 0.2, 2.5))
-    rgb, ids, _ = _trace(gs, cloud, cam, spp=4, seed=8, bg=(0.1, 0.2, 0.3))
-    _parity_ok(cloud, cam, 8, ids, rgb, 4, 1, bg=(0.1, 0.2, 0.3))
+    rgb, ids, _ = _trace(gs, cloud, cam, spp=spp, seed=8, bg=(0.1, 0.2, 0.3))
+    _parity_ok(cloud, cam, 8, ids, rgb, spp, 1, bg=(0.1, 0.2, 0.3))
 
 
 def test_full_size_sampled_parity(gs):
-    """1M-Gaussian shell, the benchmark's 1080p launch (N=1 and N=4), checked
-    on 768 sampled pixels, two thirds of them inside clusters."""
+    """1M-Gaussian shell, the benchmark's 1080p view (N=1 and N=4, per-lane
+    packets at spp 1-2 and the grouped 8-wide traversal at spp 8-16),
+    checked on 768 sampled pixels, two thirds of them inside clusters."""
     cloud = scenes.shell_cloud(0)
     cam = scenes.default_camera(1920, 1080)
     g = gs.Gaussians.from_cloud(cloud)
     bvh = gs.build_bvh(g)
-    for n_hits, spp in ((1, 2), (4, 1)):
+    for n_hits, spp in ((1, 2), (4, 1), (1, 8), (4, 16)):
         rgb, hid, _ = gs.trace_stochastic(bvh, g, cam, seed=0, spp=spp, n_hits=n_hits,
                                           want_hits=True)
         bvh.sync_status()

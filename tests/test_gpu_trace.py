@@ -62,7 +62,9 @@ def colour_ok(g, r, same):
 
 # spp picks the lanes per pixel (largest power of two <= spp, at most 32):
 # 1, 16, 4, 2 and 2 lanes here; 5 and 40 end on a partial round of samples.
-@pytest.mark.parametrize("spp,n_hits", [(1, 1), (16, 1), (4, 4), (2, 8), (3, 2), (5, 1), (40, 1)])
+# spp = 8 or more runs the grouped 8-wide traversal, (8, 8) with eight slots.
+@pytest.mark.parametrize("spp,n_hits", [(1, 1), (16, 1), (4, 4), (2, 8), (3, 2), (5, 1), (40, 1),
+                                        (8, 8)])
 def test_tiny_parity(gs, spp, n_hits):
     cloud = scenes.tiny_cloud(0)
     cam = scenes.default_camera(64, 64)
@@ -91,6 +93,19 @@ def test_passes_by_hits_invariance(gs):
     _, a, ta = _run(gs, cloud, cam, spp=8, n_hits=1, seed=9)
     _, b, tb = _run(gs, cloud, cam, spp=2, n_hits=4, seed=9)
     _, c, tc = _run(gs, cloud, cam, spp=1, n_hits=8, seed=9)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    assert np.array_equal(ta, tb) and np.array_equal(ta, tc)
+
+
+def test_grouped_and_packet_traversals_agree(gs):
+    """Sample indices 0..31 traced by 32 lanes on one pixel (grouped 8-wide
+    traversal), by 16 lanes x 2 slots (grouped) and by 4 lanes x 8 slots
+    (per-lane packets): identical hits and depths."""
+    cloud = scenes.shell_cloud(5, M=20000)
+    cam = scenes.default_camera(56, 40)
+    _, a, ta = _run(gs, cloud, cam, spp=32, n_hits=1, seed=4)
+    _, b, tb = _run(gs, cloud, cam, spp=16, n_hits=2, seed=4)
+    _, c, tc = _run(gs, cloud, cam, spp=4, n_hits=8, seed=4)
     assert np.array_equal(a, b) and np.array_equal(a, c)
     assert np.array_equal(ta, tb) and np.array_equal(ta, tc)
 
