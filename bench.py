@@ -408,15 +408,20 @@ def main():
         if events:
             events[2].record(stream)
 
-    # instrumented launches (untimed): node / primitive / shading counts
-    visits = {}
-    for n_hits, spp in ((1, SPP_N1), (4, SPP_N4)):
+    # instrumented launches (untimed): node / primitive / shading counts of
+    # the timed launches (grouped traversal: child records), and of the same
+    # rays' own traversals of the binary hierarchy (per-lane packets at spp
+    # 2, with the same per-sample hits), which define the algorithmic bytes
+    def counted(n_hits, spp):
         cnt = torch.zeros(7, dtype=torch.int64, device=dev)
         gs.trace_stochastic(bvh, g, cam, seed=0, spp=spp, n_hits=n_hits, out=rgb, counters=cnt)
         bvh.sync_status()
         c = cnt.cpu().numpy().astype(np.float64)
-        visits[n_hits] = {"nodes": c[0], "prims": c[1], "philox": c[2], "rays": c[3],
-                          "shaded": c[4], "node_fetch": c[5], "prim_fetch": c[6], "spp": spp}
+        return {"nodes": c[0], "prims": c[1], "philox": c[2], "rays": c[3],
+                "shaded": c[4], "node_fetch": c[5], "prim_fetch": c[6], "spp": spp}
+
+    visits = {1: counted(1, SPP_N1), 4: counted(4, SPP_N4)}
+    binary = {1: counted(1, 2), 4: counted(4, 2)}
 
     def timed(n_hits, spp):
         for _ in range(args.warmup):
@@ -480,14 +485,17 @@ def main():
     sh_bytes = 16 * 3 * 4
 
     def roof(v, trace_ms, n_hits):
-        # spp >= 8 on binary nodes runs the grouped 8-wide traversal, whose
-        # counters count 32-byte child records instead of 64-byte nodes
+        # algorithmic bytes per ray, from the binary hierarchy (the method's
+        # own traversal, whatever layout the kernel reads): 64 B per node
+        # entered, 64 B per Gaussian tested, one SH record per shaded sample,
+        # plus each pixel's 12-byte output
+        bv = binary[n_hits]
+        per_ray = (info["node_bytes"] * bv["nodes"] + info["prim_bytes"] * bv["prims"]
+                   + sh_bytes * bv["shaded"]) / (bv["rays"] * bv["spp"])
+        alg = per_ray * npix * v["spp"] + 12 * npix
+        # bytes the groups of the timed launch request: one 32-byte child
+        # record per fetch (spp >= 8 runs the grouped traversal)
         rec = 32 if (info["node_format"] == 0 and v["spp"] >= 8) else info["node_bytes"]
-        # per-ray algorithmic bytes: each ray's own node records and Gaussian
-        # tests, one SH record per shaded sample, the pixel's output
-        alg = (rec * v["nodes"] + info["prim_bytes"] * v["prims"]
-               + sh_bytes * v["shaded"] + 12 * npix)
-        # bytes the warps (groups) actually request: a record once per fetch
         warp = (rec * v["node_fetch"] + info["prim_bytes"] * v["prim_fetch"]
                 + sh_bytes * v["shaded"] + 12 * npix)
         ach = alg / (trace_ms * 1e-3) / 1e9
@@ -497,7 +505,9 @@ def main():
                "alg_bytes_per_launch": alg, "warp_request_bytes_per_launch": warp,
                "warp_request_gbs": warp / (trace_ms * 1e-3) / 1e9,
                "peak_kind": peak_kind, "kernel": "k_trace<%d>" % n_hits,
-               "node_record_bytes": rec}
+               "alg_bytes_per_ray": per_ray,
+               "binary_nodes_per_ray": bv["nodes"] / (bv["rays"] * bv["spp"]),
+               "gaussians_tested_per_ray": bv["prims"] / (bv["rays"] * bv["spp"])}
         if traffic is not None:
             # what DRAM actually moved (ncu counters) over this run's duration
             out["dram_gbs"] = traffic / (trace_ms * 1e-3) / 1e9

@@ -126,7 +126,7 @@ typedef struct gs_pinhole {
  *                 samples shaded with a Gaussian's colour, node records
  *                 fetched by warps, Gaussian records fetched by warps};
  *                 in the grouped traversal the first and the sixth count
- *                 32-byte child records (of the 8-wide nodes each ray
+ *                 32-byte child records (of the wide nodes each ray
  *                 enters, and that each group fetches); NULL disables
  *                 counting (the default fast path). */
 typedef struct gs_trace_params {
@@ -150,9 +150,10 @@ typedef struct gs_bvh gs_bvh;
 
 /* Node format the traversal reads (the binary tree is always built too).
  *   GS_NODES_BINARY    64-byte binary nodes, FP32 child boxes; the handle
- *                      also holds an 8-wide copy (one 32-byte FP32 record
- *                      per child, M + (M - 1) records at most) for the
- *                      grouped traversal, unless M > 2^27
+ *                      also holds 8-, 16- and 32-wide copies (one 32-byte
+ *                      FP32 record per child, M + (M - 1) records at most
+ *                      each, from 3, 4 and 5 binary levels) for the grouped
+ *                      traversal, unless M > 2^25
  *   GS_NODES_WIDE4     128-byte 4-wide nodes, FP32 child boxes
  *   GS_NODES_WIDE4_Q8  64-byte 4-wide nodes, child boxes quantised to 8 bits
  *                      per plane with outward rounding (a decoded box always
@@ -246,7 +247,7 @@ gs_status gs_bvh_export_wide(const gs_bvh *bvh, void *out, int64_t capacity, int
  * The 32 lanes of a warp split into pixels x samples: the L lanes of a pixel
  * (L the largest power of two not above spp, at most 32) trace passes
  * j*L + lane of the same ray. With L >= 8 and a GS_NODES_BINARY handle a
- * group of L lanes traverses the 8-wide copy together (each lane tests one
+ * group of L lanes traverses the L-wide copy together (each lane tests one
  * child box, evaluates one hit Gaussian's depth and alpha, and draws for its
  * own samples); otherwise each lane traverses the nodes of the handle's
  * format in a warp packet. Every form returns the same hits.

@@ -82,9 +82,14 @@ static void release(gs_bvh *b) {
     if (!b) return;
     void *bufs[] = {b->nodes, b->prims, b->status, b->codes[0], b->codes[1], b->vals[0],
                     b->vals[1], b->parent, b->arrive, b->aabb, b->bounds, b->hist,
-                    b->scan_tmp, b->wide, b->depth, b->wmap, b->wide8, b->cnt8, b->off8};
+                    b->scan_tmp, b->wide, b->depth, b->wmap, b->node_depth};
     for (void *p : bufs)
         if (p) cudaFree(p);
+    for (auto &t : b->group) {
+        if (t.rec) cudaFree(t.rec);
+        if (t.cnt) cudaFree(t.cnt);
+        if (t.off) cudaFree(t.off);
+    }
     free(b);
 }
 
@@ -137,9 +142,9 @@ gs_status gs_build_bvh_ex(const gs_gaussians *g, const gs_build_options *opt, gs
     const int64_t scan_n = 256 * tiles > nn ? 256 * tiles : nn;
     const bool wide = format != GS_NODES_BINARY;
     const size_t wide_bytes = format == GS_NODES_WIDE4 ? sizeof(Node4) : sizeof(NodeQ4);
-    // the 8-wide records of the binary format; offsets must fit 28 bits
-    const int64_t rec8 = cap + nn;
-    const bool w8 = !wide && cap > 0 && rec8 <= (int64_t)kW8OffsetMask;
+    // the W-wide records of the binary format; offsets must fit 26 bits
+    const int64_t recs = cap + nn;
+    const bool grouped = !wide && cap > 0 && recs <= (int64_t)kWideOffsetMask;
     b->node_format = format;
     struct Req { void **p; size_t bytes; } reqs[] = {
         {(void **)&b->status, 16},
@@ -158,9 +163,16 @@ gs_status gs_build_bvh_ex(const gs_gaussians *g, const gs_build_options *opt, gs
         {(void **)&b->wide, wide ? (size_t)nn * wide_bytes : 0},
         {(void **)&b->depth, wide ? (size_t)nn * 4 : 0},
         {(void **)&b->wmap, wide ? (size_t)nn * 4 : 0},
-        {(void **)&b->wide8, w8 ? (size_t)rec8 * sizeof(Child8) : 0},
-        {(void **)&b->cnt8, w8 ? (size_t)nn * 4 : 0},
-        {(void **)&b->off8, w8 ? (size_t)nn * 4 : 0},
+        {(void **)&b->node_depth, grouped ? (size_t)nn * 4 : 0},
+        {(void **)&b->group[0].rec, grouped ? (size_t)recs * sizeof(ChildRec) : 0},
+        {(void **)&b->group[0].cnt, grouped ? (size_t)nn * 4 : 0},
+        {(void **)&b->group[0].off, grouped ? (size_t)nn * 4 : 0},
+        {(void **)&b->group[1].rec, grouped ? (size_t)recs * sizeof(ChildRec) : 0},
+        {(void **)&b->group[1].cnt, grouped ? (size_t)nn * 4 : 0},
+        {(void **)&b->group[1].off, grouped ? (size_t)nn * 4 : 0},
+        {(void **)&b->group[2].rec, grouped ? (size_t)recs * sizeof(ChildRec) : 0},
+        {(void **)&b->group[2].cnt, grouped ? (size_t)nn * 4 : 0},
+        {(void **)&b->group[2].off, grouped ? (size_t)nn * 4 : 0},
     };
     int64_t total = 0;
     for (auto &r : reqs) {

@@ -549,11 +549,13 @@ __global__ void k_collapse(int64_t n_int, const Node *__restrict__ nodes,
     }
 }
 
-// The 8-wide hierarchy: one wide node per binary internal node at depth
-// 0 mod 3, whose children are its descendants three levels down, or the
-// leaves met before. Expands node i into up to 8 (reference, box) entries.
-__device__ __forceinline__ int expand8(const Node *__restrict__ nodes, uint32_t i, uint32_t ref[8],
-                                       float box[8][6]) {
+// The W-wide hierarchies (W = 2^LEVELS): one wide node per binary internal
+// node at depth 0 mod LEVELS, whose children are its descendants LEVELS
+// levels down, or the leaves met before. expand_wide lists them, left to
+// right, with their boxes.
+template <int LEVELS>
+__device__ __forceinline__ int expand_wide(const Node *__restrict__ nodes, uint32_t i,
+                                           uint32_t ref[1 << LEVELS], float box[1 << LEVELS][6]) {
     int n = 0;
     const Node nd = nodes[i];
     for (int sd = 0; sd < 2; ++sd) {
@@ -561,7 +563,7 @@ __device__ __forceinline__ int expand8(const Node *__restrict__ nodes, uint32_t 
         for (int q = 0; q < 6; ++q) box[n][q] = nd.box[sd][q];
         ++n;
     }
-    for (int level = 1; level < 3; ++level) {
+    for (int level = 1; level < LEVELS; ++level) {
         // expand in place from the back so entries keep left-to-right order
         int m = n;
         for (int j = 0; j < n; ++j)
@@ -585,11 +587,9 @@ __device__ __forceinline__ int expand8(const Node *__restrict__ nodes, uint32_t 
     return n;
 }
 
-// Children of the wide node at each binary internal node (0 where none);
-// the same count seeds the offsets.
-__global__ void k_count8(int64_t n_int, const Node *__restrict__ nodes,
-                         const uint32_t *__restrict__ parent_int, uint32_t *__restrict__ cnt,
-                         uint32_t *__restrict__ off) {
+// Depth of every binary internal node (walk to the root).
+__global__ void k_node_depth(int64_t n_int, const uint32_t *__restrict__ parent_int,
+                             uint32_t *__restrict__ depth) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_int) return;
     uint32_t d = 0, p = (uint32_t)i;
@@ -597,31 +597,43 @@ __global__ void k_count8(int64_t n_int, const Node *__restrict__ nodes,
         p = parent_int[p];
         ++d;
     }
+    depth[i] = d;
+}
+
+// Children of the wide node at each binary internal node (0 where none);
+// the same count seeds the offsets.
+template <int LEVELS>
+__global__ void k_count_wide(int64_t n_int, const Node *__restrict__ nodes,
+                             const uint32_t *__restrict__ depth, uint32_t *__restrict__ cnt,
+                             uint32_t *__restrict__ off) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
     uint32_t c = 0;
-    if (d % 3u == 0u) {
-        uint32_t ref[8];
-        float box[8][6];
-        c = (uint32_t)expand8(nodes, (uint32_t)i, ref, box);
+    if (depth[i] % (uint32_t)LEVELS == 0u) {
+        uint32_t ref[1 << LEVELS];
+        float box[1 << LEVELS][6];
+        c = (uint32_t)expand_wide<LEVELS>(nodes, (uint32_t)i, ref, box);
     }
     cnt[i] = c;
     off[i] = c;
 }
 
 // Writes the child records of every wide node at its offset.
-__global__ void k_collapse8(int64_t n_int, const Node *__restrict__ nodes,
-                            const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ off,
-                            Child8 *__restrict__ rec) {
+template <int LEVELS>
+__global__ void k_collapse_wide(int64_t n_int, const Node *__restrict__ nodes,
+                                const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ off,
+                                ChildRec *__restrict__ rec) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_int || cnt[i] == 0u) return;
-    uint32_t ref[8];
-    float box[8][6];
-    const int n = expand8(nodes, (uint32_t)i, ref, box);
-    Child8 *dst = rec + off[i];
+    uint32_t ref[1 << LEVELS];
+    float box[1 << LEVELS][6];
+    const int n = expand_wide<LEVELS>(nodes, (uint32_t)i, ref, box);
+    ChildRec *dst = rec + off[i];
     for (int j = 0; j < n; ++j) {
-        Child8 c;
+        ChildRec c;
         for (int q = 0; q < 3; ++q) { c.lo[q] = box[j][q]; c.hi[q] = box[j][3 + q]; }
         const uint32_t r = ref[j];
-        c.child = (r & kLeafBit) ? r : (((cnt[r] - 1u) << kW8CountShift) | off[r]);
+        c.child = (r & kLeafBit) ? r : (((cnt[r] - 1u) << kWideCountShift) | off[r]);
         c.reserved = 0;
         dst[j] = c;
     }
@@ -693,12 +705,19 @@ gs_status build_into(gs_bvh *b, const gs_gaussians *g, cudaStream_t s) {
             k_collapse<GS_NODES_WIDE4_Q8><<<grid_for(n_int, 256), 256, 0, s>>>(
                 n_int, b->nodes, b->depth, b->wmap, b->wide);
     }
-    if (b->wide8) {
+    if (b->node_depth) {
         const int64_t n_int = b->n_nodes;
-        k_count8<<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->nodes, b->parent, b->cnt8, b->off8);
-        scan_exclusive(b->off8, n_int, b->scan_tmp, s);
-        k_collapse8<<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->nodes, b->cnt8, b->off8,
-                                                         b->wide8);
+        k_node_depth<<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->parent, b->node_depth);
+        const GroupTree *t = b->group;
+        k_count_wide<3><<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->nodes, b->node_depth, t[0].cnt, t[0].off);
+        scan_exclusive(t[0].off, n_int, b->scan_tmp, s);
+        k_collapse_wide<3><<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->nodes, t[0].cnt, t[0].off, t[0].rec);
+        k_count_wide<4><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, b->node_depth, t[1].cnt, t[1].off);
+        scan_exclusive(t[1].off, n_int, b->scan_tmp, s);
+        k_collapse_wide<4><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, t[1].cnt, t[1].off, t[1].rec);
+        k_count_wide<5><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, b->node_depth, t[2].cnt, t[2].off);
+        scan_exclusive(t[2].off, n_int, b->scan_tmp, s);
+        k_collapse_wide<5><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, t[2].cnt, t[2].off, t[2].rec);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "build launch");
     return GS_OK;

@@ -43,19 +43,29 @@ struct __align__(16) Node4 {
 };
 static_assert(sizeof(Node4) == 128, "Node4 must be 128 bytes");
 
-// Child record of the 8-wide hierarchy, 32 bytes, one lane's load. A wide
-// node is the run of its children's records (2 to 8) at its offset; an
-// internal child is referenced as (count - 1) << 28 | offset, a leaf as
-// kLeafBit | primitive index.
-struct __align__(16) Child8 {
+// Child record of the W-wide hierarchies (W = 8, 16, 32) that groups of W
+// lanes traverse, 32 bytes, one lane's load. A wide node is the run of its
+// children's records (2 to W) at its offset; an internal child is
+// referenced as (count - 1) << 26 | offset, a leaf as kLeafBit | primitive
+// index.
+struct __align__(16) ChildRec {
     float lo[3];
     float hi[3];
     uint32_t child;
     uint32_t reserved;
 };
-static_assert(sizeof(Child8) == 32, "Child8 must be 32 bytes");
-constexpr int kW8CountShift = 28;
-constexpr uint32_t kW8OffsetMask = (1u << kW8CountShift) - 1u;
+static_assert(sizeof(ChildRec) == 32, "ChildRec must be 32 bytes");
+constexpr int kWideCountShift = 26;
+constexpr uint32_t kWideOffsetMask = (1u << kWideCountShift) - 1u;
+constexpr int kGroupTrees = 3;  // W = 8 << i: collapses of 3, 4 and 5 binary levels
+
+// One W-wide hierarchy: records, and per binary internal node the child
+// count of the wide node there (0 where none) and its first record.
+struct GroupTree {
+    ChildRec *rec;
+    uint32_t *cnt;
+    uint32_t *off;
+};
 
 // 4-wide node, 64 bytes, child boxes quantised to 8 bits per plane against
 // the node's own box: plane = origin[a] + q * 2^exp[a], with the lower
@@ -116,10 +126,10 @@ struct gs_bvh {
     void *wide;         // Node4 or NodeQ4 array, compact
     uint32_t *depth;    // depth of every internal binary node
     uint32_t *wmap;     // binary internal node -> wide node index
-    // 8-wide hierarchy for groups of lanes sharing one ray (binary format)
-    gsrt::Child8 *wide8;  // child records, at most M + (M - 1)
-    uint32_t *cnt8;       // children of the wide node at each binary node (0: none)
-    uint32_t *off8;       // its first record
+    // W-wide hierarchies for groups of lanes sharing one ray (binary format
+    // only): W = 8, 16, 32, each at most M + (M - 1) records
+    gsrt::GroupTree group[gsrt::kGroupTrees];
+    uint32_t *node_depth;  // depth of every binary internal node
 };
 
 namespace gsrt {

@@ -36,16 +36,18 @@
 namespace gsrt {
 namespace {
 
-// Template value of FMT for the cooperative traversal of the 8-wide records
-// (groups of 8 or more lanes on one pixel); the others are GS_NODES_*.
-constexpr int kFmtCoop8 = 8;
+// Template values of FMT for the cooperative traversal of the W-wide records
+// by groups of W = 8, 16, 32 lanes on one pixel (kFmtGroup + log2 W); the
+// others are GS_NODES_*.
+constexpr int kFmtGroup = 8;
+__host__ __device__ constexpr bool is_group_fmt(int f) { return f >= kFmtGroup + 3; }
 
 // Persistent kernel: each warp repeatedly takes the next tile (one atomic
 // per tile, so the tail of the launch stays balanced), then runs all passes
 // of its pixels. The cooperative form is latency-bound and is built for
 // eight resident blocks per SM (five with eight slots per lane).
 template <int N, bool COUNT, int FMT>
-__global__ void __launch_bounds__(kThreads, FMT == kFmtCoop8 ? (N >= 8 ? 5 : kCoopMinBlocks) : 1)
+__global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? (N >= 8 ? 5 : kGroupMinBlocks) : 1)
     k_trace(const TraceArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;
@@ -61,12 +63,14 @@ __global__ void __launch_bounds__(kThreads, FMT == kFmtCoop8 ? (N >= 8 ? 5 : kCo
     uint32_t err = 0;
     Counts cnt;
     unsigned long long n_shaded = 0, n_rays = 0;
-    constexpr bool coop = FMT == kFmtCoop8;
-    __shared__ uint32_t s_ref[coop ? kThreads / 32 : 1][kCoopGroupsPerWarp][coop ? kCoopStack : 1];
-    __shared__ float s_t[coop ? kThreads / 32 : 1][kCoopGroupsPerWarp][coop ? kCoopStack : 1];
-    const int grp = coop ? (lane >> lg) : 0;
-    uint32_t *grp_ref = s_ref[coop ? threadIdx.x >> 5 : 0][grp];
-    float *grp_t = s_t[coop ? threadIdx.x >> 5 : 0][grp];
+    // group stacks: each warp's pool split evenly among its groups
+    constexpr bool grouped = is_group_fmt(FMT);
+    constexpr int LG = grouped ? FMT - kFmtGroup : 3;
+    __shared__ uint32_t s_ref[grouped ? kThreads / 32 : 1][grouped ? kGroupPool : 1];
+    __shared__ float s_t[grouped ? kThreads / 32 : 1][grouped ? kGroupPool : 1];
+    const int grp_off = grouped ? (lane >> LG) * (kGroupPool >> (5 - LG)) : 0;
+    uint32_t *grp_ref = s_ref[grouped ? threadIdx.x >> 5 : 0] + grp_off;
+    float *grp_t = s_t[grouped ? threadIdx.x >> 5 : 0] + grp_off;
     for (;;) {
         uint32_t tile = 0;
         if (lane == 0) tile = atomicAdd(a.work, 1u);
@@ -97,8 +101,8 @@ __global__ void __launch_bounds__(kThreads, FMT == kFmtCoop8 ? (N >= 8 ? 5 : kCo
             update_clip(r, a.t_max);
             if (!live) r.t_far = -INFINITY;  // lanes off the image never hit
             if (a.n_nodes > 0) {
-                if constexpr (coop)
-                    traverse_coop8<N, COUNT>(a, r, pass, lg, grp_ref, grp_t, err, cnt);
+                if constexpr (grouped)
+                    traverse_group<N, COUNT, LG>(a, r, pass, grp_ref, grp_t, err, cnt);
                 else if constexpr (FMT == GS_NODES_BINARY)
                     traverse_packet<N, COUNT>(a, r, pass, stack, stack_t, err, cnt);
                 else
@@ -182,8 +186,11 @@ gs_status launch_nf(const TraceArgs &a, bool count, cudaStream_t s) {
 template <int N>
 gs_status launch_n(const TraceArgs &a, int format, bool count, cudaStream_t s) {
     // groups of 8 or more lanes on one pixel take the cooperative form
-    if (format == GS_NODES_BINARY && a.wide8 != nullptr && a.lpp_log2 >= 3)
-        return launch_nf<N, kFmtCoop8>(a, count, s);
+    if (format == GS_NODES_BINARY && a.grec != nullptr) {
+        if (a.lpp_log2 == 5) return launch_nf<N, kFmtGroup + 5>(a, count, s);
+        if (a.lpp_log2 == 4) return launch_nf<N, kFmtGroup + 4>(a, count, s);
+        if (a.lpp_log2 == 3) return launch_nf<N, kFmtGroup + 3>(a, count, s);
+    }
     switch (format) {
         case GS_NODES_WIDE4: return launch_nf<N, GS_NODES_WIDE4>(a, count, s);
         case GS_NODES_WIDE4_Q8: return launch_nf<N, GS_NODES_WIDE4_Q8>(a, count, s);
@@ -199,8 +206,14 @@ gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole 
     TraceArgs a;
     a.nodes = b->nodes;
     a.wide = b->wide;
-    a.wide8 = b->wide8;
-    a.cnt8 = b->cnt8;
+    a.lpp_log2 = lanes_per_pixel_log2(p->spp);
+    if (b->node_depth && a.lpp_log2 >= 3) {
+        a.grec = b->group[a.lpp_log2 - 3].rec;
+        a.gcnt = b->group[a.lpp_log2 - 3].cnt;
+    } else {
+        a.grec = nullptr;
+        a.gcnt = nullptr;
+    }
     a.prims = b->prims;
     a.sh = g->sh;
     a.n_nodes = b->n_nodes;
@@ -231,7 +244,6 @@ gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole 
     a.counters = p->counters;
     a.status = b->status;
     a.work = b->status + 1;
-    a.lpp_log2 = lanes_per_pixel_log2(p->spp);
     a.depth_mode = p->depth_mode;
     a.rng_mode = p->rng_mode;
     {

@@ -19,8 +19,8 @@ constexpr int kThreads = 128;
 struct TraceArgs {
     const Node *nodes;
     const void *wide;  // Node4 or NodeQ4 when the handle has wide nodes
-    const Child8 *wide8;   // 8-wide child records (binary format), or null
-    const uint32_t *cnt8;  // their per-node child counts (root at 0)
+    const ChildRec *grec;  // W-wide records for the launch's group size, or null
+    const uint32_t *gcnt;  // their per-node child counts (the root's at 0)
     const PrimRec *prims;
     const void *sh;
     int64_t n_nodes;
@@ -715,34 +715,36 @@ __device__ __forceinline__ void traverse_packet_wide(const TraceArgs &a, Ray<N> 
 
 
 // ---------------------------------------------------------------- groups
-constexpr int kCoopStack = 128;       // stack entries per group of lanes
-constexpr int kCoopGroupsPerWarp = 4; // groups of 8 or more lanes
-constexpr int kCoopMinBlocks = 8;     // resident blocks per SM to build for
+constexpr int kGroupPool = 512;    // stack entries per warp, split among its groups
+constexpr int kGroupMinBlocks = 8; // resident blocks per SM to build for
 
-// Cooperative traversal of the 8-wide hierarchy by a group of L = 2^lg >= 8
-// lanes that trace different samples of one ray. The group visits a wide
-// node in one step: lane k tests child k against the group's clip (the
-// farthest of its lanes' clips). Lanes holding a hit leaf evaluate the
-// sample-independent part of Alg. 1 for it (cand_depth, cand_alpha); every
-// lane then draws for its own samples against each candidate (accept). The
-// nearest hit inner child is visited next and the other hit inner children
-// go to the group's stack in shared memory. Every node and leaf a lane's
-// own ray needs is visited, and each lane keeps its own slots and clip, so
-// per-lane results are those of an independent traversal.
-template <int N, bool COUNT>
-__device__ __forceinline__ void traverse_coop8(const TraceArgs &a, Ray<N> &r, int pass, int lg,
+// Cooperative traversal of the W-wide hierarchy (W = L = 2^LG, 8 to 32) by a
+// group of L lanes that trace different samples of one ray. The group
+// visits a wide node in one step: lane k tests child k against the group's
+// clip (the farthest of its lanes' clips). Lanes holding a hit leaf evaluate
+// the sample-independent part of Alg. 1 for it (cand_depth, cand_alpha);
+// every lane then draws for its own samples against each candidate
+// (accept). The nearest hit inner child is visited next and the other hit
+// inner children go to the group's stack in shared memory. Every node and
+// leaf a lane's own ray needs is visited, and each lane keeps its own slots
+// and clip, so per-lane results are those of an independent traversal.
+template <int N, bool COUNT, int LG>
+__device__ __forceinline__ void traverse_group(const TraceArgs &a, Ray<N> &r, int pass,
                                                uint32_t *s_ref, float *s_t, uint32_t &err,
                                                Counts &cnt) {
+    constexpr int L = 1 << LG;
+    constexpr int kCap = kGroupPool >> (5 - LG);  // this group's stack entries
+    constexpr uint32_t kLaneBits = L == 32 ? 0xffffffffu : ((1u << (L & 31)) - 1u);
     const int lane = threadIdx.x & 31;
-    const int L = 1 << lg;
     const int base = lane & ~(L - 1);
     const int sub = lane & (L - 1);
-    const uint32_t gmask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << base);
+    const uint32_t gmask = kLaneBits << base;
     float G = r.t_far >= r.t_min ? r.t_far : -INFINITY;
+#pragma unroll
     for (int o = 1; o < L; o <<= 1) G = fmaxf(G, __shfl_xor_sync(gmask, G, o));
     if (!(G >= r.t_min)) return;  // no lane of the group is live
     int sp = 0;
-    uint32_t node = (__ldg(a.cnt8) - 1u) << kW8CountShift;  // the root's records start at 0
+    uint32_t node = (__ldg(a.gcnt) - 1u) << kWideCountShift;  // the root's records start at 0
     uint32_t steps = 0;
     float node_t = r.t_min;
     for (;;) {
@@ -750,7 +752,7 @@ __device__ __forceinline__ void traverse_coop8(const TraceArgs &a, Ray<N> &r, in
             err |= kErrSteps;
             break;
         }
-        const int n_child = (int)(node >> kW8CountShift) + 1;
+        const int n_child = (int)((node >> kWideCountShift) & 31u) + 1;
         if (COUNT) {
             // the child records of a wide node this lane's own ray enters
             cnt.nodes += node_t <= r.t_far ? n_child : 0;
@@ -761,17 +763,17 @@ __device__ __forceinline__ void traverse_coop8(const TraceArgs &a, Ray<N> &r, in
         bool hit = false;
         if (sub < n_child) {
             const float4 *cp =
-                reinterpret_cast<const float4 *>(a.wide8 + (node & kW8OffsetMask) + sub);
+                reinterpret_cast<const float4 *>(a.grec + (node & kWideOffsetMask) + sub);
             const float4 q0 = __ldg(cp), q1 = __ldg(cp + 1);
             const float bx[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
             ref = __float_as_uint(q1.z);
             hit = slab(bx, r.inv, r.oinv, r.t_min, G, te);
         }
         const bool leaf = (ref & kLeafBit) != 0u;
-        const unsigned lm = (__ballot_sync(gmask, hit && leaf) >> base) & 0xffu;
+        const uint32_t lm = (__ballot_sync(gmask, hit && leaf) >> base) & kLaneBits;
         if (lm) {
             if (COUNT) {
-                for (unsigned m2 = lm; m2; m2 &= m2 - 1u) {
+                for (uint32_t m2 = lm; m2; m2 &= m2 - 1u) {
                     const float tl = __shfl_sync(gmask, te, base + __ffs(m2) - 1);
                     cnt.prims += tl <= r.t_far;
                     cnt.prim_fetch += lane == base;
@@ -790,7 +792,7 @@ __device__ __forceinline__ void traverse_coop8(const TraceArgs &a, Ray<N> &r, in
                 cgid = c.gid;
             }
             // every lane: its own draws against each candidate
-            for (unsigned cm = (__ballot_sync(gmask, ok) >> base) & 0xffu; cm; cm &= cm - 1u) {
+            for (uint32_t cm = (__ballot_sync(gmask, ok) >> base) & kLaneBits; cm; cm &= cm - 1u) {
                 const int src = base + __ffs(cm) - 1;
                 const float t = __shfl_sync(gmask, ct, src);
                 const float key_tc = __shfl_sync(gmask, ck1, src);
@@ -802,22 +804,23 @@ __device__ __forceinline__ void traverse_coop8(const TraceArgs &a, Ray<N> &r, in
                     accept<N, COUNT>(a, r, pass, closer, t, key_tc, key_tau, alpha, gid, cnt.draws);
             }
             G = r.t_far >= r.t_min ? r.t_far : -INFINITY;
+#pragma unroll
             for (int o = 1; o < L; o <<= 1) G = fmaxf(G, __shfl_xor_sync(gmask, G, o));
         }
         const bool inner = hit && !leaf && te <= G;
-        const unsigned im = (__ballot_sync(gmask, inner) >> base) & 0xffu;
+        const uint32_t im = (__ballot_sync(gmask, inner) >> base) & kLaneBits;
         if (im) {
-            // nearest inner child next (ties and the low three mantissa
-            // bits of the entry distance broken by child index)
+            // nearest inner child next (ties and the low five mantissa bits
+            // of the entry distance broken by child index)
             const uint32_t key = __reduce_min_sync(
-                gmask, inner ? ((__float_as_uint(fmaxf(te, 0.0f)) & ~7u) | (uint32_t)sub)
+                gmask, inner ? ((__float_as_uint(fmaxf(te, 0.0f)) & ~31u) | (uint32_t)sub)
                              : 0xffffffffu);
-            const int nj = (int)(key & 7u);
+            const int nj = (int)(key & 31u);
             const uint32_t next = __shfl_sync(gmask, ref, base + nj);
             const float next_t = __shfl_sync(gmask, te, base + nj);
-            const unsigned others = im & ~(1u << nj);
+            const uint32_t others = im & ~(1u << nj);
             const int npush = __popc(others);
-            if (sp + npush > kCoopStack) {
+            if (sp + npush > kCap) {
                 err |= kErrStack;
                 break;
             }
