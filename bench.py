@@ -477,7 +477,11 @@ def main():
 
     rays_step = npix * SPP_N1 * world
     value = rays_step / (r1["step_ms"] * 1e-3) / 1e6
-    launches_per_step = 29
+    # this library's kernels per step: the rebuild (preprocess, key, 8 radix
+    # passes of histogram + 3-kernel scan + scatter, Karras, leaves, node
+    # depths, and count + 3-kernel scan + collapse for each of the three
+    # wide copies) and one trace
+    launches_per_step = 2 + 8 * 5 + 2 + 1 + 3 * 5 + 1
 
     # roofline of the trace kernel: algorithmic bytes per launch / duration
     peak, peak_kind = measured_peak()
