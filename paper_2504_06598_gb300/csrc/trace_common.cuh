@@ -714,6 +714,76 @@ __device__ __forceinline__ void traverse_packet_wide(const TraceArgs &a, Ray<N> 
 }
 
 
+// Independent traversal of the binary hierarchy by one lane (for rays
+// whose directions differ from lane to lane, where a packet would visit the
+// union of unrelated paths): near child first, the other pushed with its
+// entry distance, pops skipped once the lane's clip has passed them.
+template <int N, bool COUNT>
+__device__ __forceinline__ void traverse_lane(const TraceArgs &a, Ray<N> &r, int pass,
+                                              uint32_t *stack, float *stack_t, uint32_t &err,
+                                              Counts &cnt) {
+    if (!(r.t_far >= r.t_min)) return;
+    int sp = 0;
+    uint32_t node = 0, steps = 0;
+    for (;;) {
+        if (++steps > a.step_limit) {
+            err |= kErrSteps;
+            break;
+        }
+        if (COUNT) {
+            ++cnt.nodes;
+            ++cnt.node_fetch;
+        }
+        const float4 *np = reinterpret_cast<const float4 *>(a.nodes + node);
+        const float4 b0 = __ldg(np), b1 = __ldg(np + 1), b2 = __ldg(np + 2);
+        const uint4 cref = __ldg(reinterpret_cast<const uint4 *>(np + 3));
+        const float boxL[6] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
+        const float boxR[6] = {b1.z, b1.w, b2.x, b2.y, b2.z, b2.w};
+        float tL, tR;
+        bool hL = slab(boxL, r.inv, r.oinv, r.t_min, r.t_far, tL);
+        bool hR = slab(boxR, r.inv, r.oinv, r.t_min, r.t_far, tR);
+        const bool leafL = (cref.x & kLeafBit) != 0u, leafR = (cref.y & kLeafBit) != 0u;
+        if ((leafL && hL) || (leafR && hR)) {
+            const bool swap = leafL && leafR && hR && (!hL || tR < tL);
+            for (int li = 0; li < 2; ++li) {
+                const bool right = (li == 0) == swap;
+                if (!(right ? leafR : leafL) || !(right ? hR : hL)) continue;
+                if (COUNT) {
+                    ++cnt.prims;
+                    ++cnt.prim_fetch;
+                }
+                intersect<N, COUNT>(a, r, (right ? cref.y : cref.x) & ~kLeafBit, pass, cnt.draws);
+            }
+        }
+        hL = hL && !leafL && tL <= r.t_far;
+        hR = hR && !leafR && tR <= r.t_far;
+        if (hL && hR) {
+            if (sp >= a.stack_depth) {
+                err |= kErrStack;
+                break;
+            }
+            const bool left_first = tL <= tR;
+            stack[sp] = left_first ? cref.y : cref.x;
+            stack_t[sp] = left_first ? tR : tL;
+            ++sp;
+            node = left_first ? cref.x : cref.y;
+            continue;
+        }
+        if (hL) { node = cref.x; continue; }
+        if (hR) { node = cref.y; continue; }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (stack_t[sp] <= r.t_far) {
+                node = stack[sp];
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+    }
+}
+
 // ---------------------------------------------------------------- groups
 constexpr int kGroupPool = 512;    // stack entries per warp, split among its groups
 constexpr int kGroupMinBlocks = 8; // resident blocks per SM to build for

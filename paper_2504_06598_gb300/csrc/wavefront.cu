@@ -94,11 +94,45 @@ __device__ __forceinline__ void trace_packet(const TraceArgs &a, Ray<1> &r, int 
     else traverse_packet_wide<1, COUNT, FMT>(a, r, pass, stack, stack_t, err, cnt);
 }
 
-template <int FMT, int STACK, bool COUNT>
+// Bounce rays leave each lane in its own direction: on binary nodes each
+// lane traverses alone instead of as a packet.
+template <int FMT, bool COUNT>
+__device__ __forceinline__ void trace_own_ray(const TraceArgs &a, Ray<1> &r, int pass,
+                                              uint32_t *stack, float *stack_t, uint32_t &err,
+                                              Counts &cnt) {
+    if (a.n_nodes == 0) return;
+    if (FMT == GS_NODES_BINARY) traverse_lane<1, COUNT>(a, r, pass, stack, stack_t, err, cnt);
+    else traverse_packet_wide<1, COUNT, FMT>(a, r, pass, stack, stack_t, err, cnt);
+}
+
+// Camera and shadow rays are one ray for all lanes of a pixel: with groups
+// of 2^GLG >= 8 lanes they take the grouped traversal of the wide copy.
+template <int FMT, int GLG, bool COUNT>
+__device__ __forceinline__ void trace_pixel_ray(const TraceArgs &a, Ray<1> &r, int pass,
+                                                uint32_t *stack, float *stack_t, uint32_t *g_ref,
+                                                float *g_t, uint32_t &err, Counts &cnt) {
+    if (a.n_nodes == 0) return;
+    if constexpr (GLG >= 3) traverse_group<1, COUNT, GLG>(a, r, pass, g_ref, g_t, err, cnt);
+    else trace_packet<FMT, COUNT>(a, r, pass, stack, stack_t, err, cnt);
+}
+
+// GLG: log2 of the lanes per pixel when the grouped traversal is used, else
+// 0. The group stacks are dynamic shared memory: per warp kGroupPool
+// references then kGroupPool entry distances.
+template <int FMT, int STACK, bool COUNT, int GLG>
 __global__ void k_render_views(const WaveArgs w) {
     const TraceArgs &a = w.t;
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;
+    extern __shared__ uint32_t wave_smem[];
+    uint32_t *g_ref = nullptr;
+    float *g_t = nullptr;
+    if constexpr (GLG >= 3) {
+        uint32_t *pool = wave_smem + (size_t)(threadIdx.x >> 5) * 2 * kGroupPool;
+        const int off = (lane >> GLG) * (kGroupPool >> (5 - GLG));
+        g_ref = pool + off;
+        g_t = reinterpret_cast<float *>(pool + kGroupPool) + off;
+    }
     const int lg = a.lpp_log2, L = 1 << lg;
     const int tw_lg = tile_w_log2(lg), th_lg = 5 - lg - tw_lg;
     const int sub = lane & (L - 1), pl = lane >> lg;
@@ -154,7 +188,7 @@ __global__ void k_render_views(const WaveArgs w) {
             reset_slots(r);
             update_clip(r, r.t_max);
             if (!live) r.t_far = -INFINITY;
-            trace_packet<FMT, COUNT>(a, r, s, stack, stack_t, err, cnt);
+            trace_pixel_ray<FMT, GLG, COUNT>(a, r, s, stack, stack_t, g_ref, g_t, err, cnt);
             n_cam += live;
             const bool gauss = live && r.slot[0].gid != 0xffffffffu && r.slot[0].t < tq;
             const bool on_ground = live && ground && !gauss;
@@ -179,8 +213,11 @@ __global__ void k_render_views(const WaveArgs w) {
                 for (int i = 0; i < 3; ++i) omega[i] = __fdiv_rn(wl[i], dist);
                 const bool need = on_ground && omega[1] > 0.0f && dist2 > 0.0f;
                 if (!__any_sync(kAll, need)) continue;
+                // one ray for the pixel's lanes (the grouped traversal tests
+                // each child against the group's ray)
+                const bool pix_ok = ground && dist2 > 0.0f;
                 Ray<1> sr;
-                set_ray(sr, p, need ? omega : d0);
+                set_ray(sr, p, pix_ok ? omega : d0);
                 sr.ray_id = ray_id;
                 sr.stream_tag = kTagShadow + (uint32_t)l;
                 sr.t_min = w.eps;
@@ -189,7 +226,7 @@ __global__ void k_render_views(const WaveArgs w) {
                 reset_slots(sr);
                 update_clip(sr, sr.t_max);
                 if (!need) sr.t_far = -INFINITY;
-                trace_packet<FMT, COUNT>(a, sr, s, stack, stack_t, err, cnt);
+                trace_pixel_ray<FMT, GLG, COUNT>(a, sr, s, stack, stack_t, g_ref, g_t, err, cnt);
                 n_shadow += need;
                 if (need && sr.slot[0].gid == 0xffffffffu) {
                     diag_vis |= 1 << l;
@@ -214,7 +251,7 @@ __global__ void k_render_views(const WaveArgs w) {
                     reset_slots(br);
                     update_clip(br, br.t_max);
                     if (!need) br.t_far = -INFINITY;
-                    trace_packet<FMT, COUNT>(a, br, s, stack, stack_t, err, cnt);
+                    trace_own_ray<FMT, COUNT>(a, br, s, stack, stack_t, err, cnt);
                     n_bounce += need;
                     if (need) {
                         float lb[3] = {a.bg[0], a.bg[1], a.bg[2]};
@@ -264,14 +301,15 @@ __global__ void k_render_views(const WaveArgs w) {
     }
 }
 
-template <int FMT, int STACK, bool COUNT>
+template <int FMT, int STACK, bool COUNT, int GLG>
 gs_status launch_views(const WaveArgs &w, int threads, cudaStream_t s) {
     int dev = 0, sms = 0, per = 0;
+    const size_t smem = GLG >= 3 ? (size_t)(threads / 32) * 2 * kGroupPool * sizeof(uint32_t) : 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_render_views<FMT, STACK, COUNT>,
-                                                          threads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per, k_render_views<FMT, STACK, COUNT, GLG>, threads, smem);
     if (e != cudaSuccess) return cuda_fail(e, "render launch setup");
     const uint32_t warps_per_block = (uint32_t)threads / 32;
     uint32_t blocks = (uint32_t)sms * (uint32_t)(per > 0 ? per : 1);
@@ -280,16 +318,37 @@ gs_status launch_views(const WaveArgs &w, int threads, cudaStream_t s) {
     if (blocks == 0) return GS_OK;
     if ((e = cudaMemsetAsync(w.t.work, 0, sizeof(uint32_t), s)) != cudaSuccess)
         return cuda_fail(e, "reset work counter");
-    k_render_views<FMT, STACK, COUNT><<<blocks, threads, 0, s>>>(w);
+    k_render_views<FMT, STACK, COUNT, GLG><<<blocks, threads, smem, s>>>(w);
     return GS_OK;
+}
+
+template <int FMT, int GLG>
+gs_status launch_views_g(const WaveArgs &w, int threads, int stack, cudaStream_t s) {
+    const bool count = w.counters != nullptr;
+    if (stack == 48)
+        return count ? launch_views<FMT, 48, true, GLG>(w, threads, s)
+                     : launch_views<FMT, 48, false, GLG>(w, threads, s);
+    return count ? launch_views<FMT, 96, true, GLG>(w, threads, s)
+                 : launch_views<FMT, 96, false, GLG>(w, threads, s);
 }
 
 template <int FMT>
 gs_status launch_views_f(const WaveArgs &w, int threads, int stack, cudaStream_t s) {
-    const bool count = w.counters != nullptr;
-    if (stack == 48)
-        return count ? launch_views<FMT, 48, true>(w, threads, s) : launch_views<FMT, 48, false>(w, threads, s);
-    return count ? launch_views<FMT, 96, true>(w, threads, s) : launch_views<FMT, 96, false>(w, threads, s);
+    return launch_views_g<FMT, 0>(w, threads, stack, s);
+}
+
+// Binary handles with wide copies: pixels with 8 or more lanes group.
+template <>
+gs_status launch_views_f<GS_NODES_BINARY>(const WaveArgs &w, int threads, int stack, cudaStream_t s) {
+    if (w.t.grec != nullptr) {
+        switch (w.t.lpp_log2) {
+            case 5: return launch_views_g<GS_NODES_BINARY, 5>(w, threads, stack, s);
+            case 4: return launch_views_g<GS_NODES_BINARY, 4>(w, threads, stack, s);
+            case 3: return launch_views_g<GS_NODES_BINARY, 3>(w, threads, stack, s);
+            default: break;
+        }
+    }
+    return launch_views_g<GS_NODES_BINARY, 0>(w, threads, stack, s);
 }
 
 }  // namespace
@@ -321,6 +380,10 @@ gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_p
     a.status = b->status;
     a.work = b->status + 1;
     a.lpp_log2 = lanes_per_pixel_log2(p->spp);
+    if (b->node_depth && a.lpp_log2 >= 3) {
+        a.grec = b->group[a.lpp_log2 - 3].rec;
+        a.gcnt = b->group[a.lpp_log2 - 3].cnt;
+    }
     const int tw_lg = tile_w_log2(a.lpp_log2), th_lg = 5 - a.lpp_log2 - tw_lg;
     uint32_t tiles = 0;
     int64_t pix = 0;

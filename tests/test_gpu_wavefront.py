@@ -35,9 +35,11 @@ def _items(cams):
     return [(v, p) for v, c in enumerate(cams) for p in range(c.width * c.height)]
 
 
-def test_parity_with_oracle(gs):
+# spp 3: per-lane packets; 8 and 32: camera and shadow rays take the grouped
+# traversal (8 and 32 lanes on one pixel), bounce rays per-lane packets.
+@pytest.mark.parametrize("spp", [3, 8, 32])
+def test_parity_with_oracle(gs, spp):
     cloud, cams, ex = _setup()
-    spp = 3
     g = gs.Gaussians.from_cloud(cloud)
     bvh = gs.build_bvh(g)
     rgb, smp = gs.render_views(bvh, g, cams, ex, seed=5, spp=spp, bg=(0.05, 0.1, 0.2),
@@ -58,14 +60,15 @@ def test_parity_with_oracle(gs):
     assert err.max() <= 0.0, err.max()
 
 
-def test_formats_and_launch_shapes_agree(gs):
+@pytest.mark.parametrize("spp", [2, 16])
+def test_formats_and_launch_shapes_agree(gs, spp):
     cloud, cams, ex = _setup()
     g = gs.Gaussians.from_cloud(cloud)
     results = []
     for fmt in ("binary", "wide4", "wide4_q8"):
         bvh = gs.build_bvh(g, node_format=fmt)
         for block, stack in ((128, 96), (64, 48), (256, 96)):
-            rgb, smp = gs.render_views(bvh, g, cams, ex, seed=1, spp=2, block_threads=block,
+            rgb, smp = gs.render_views(bvh, g, cams, ex, seed=1, spp=spp, block_threads=block,
                                        stack_entries=stack, want_samples=True)
             results.append((rgb.cpu().numpy(), smp.cpu().numpy()))
         bvh.sync_status()
@@ -74,14 +77,15 @@ def test_formats_and_launch_shapes_agree(gs):
         assert np.array_equal(rgb, results[0][0]) and np.array_equal(smp, results[0][1])
 
 
-def test_without_extras_matches_single_view_traces(gs):
+@pytest.mark.parametrize("spp", [4, 16])
+def test_without_extras_matches_single_view_traces(gs, spp):
     cloud, cams, _ = _setup()
     g = gs.Gaussians.from_cloud(cloud)
     bvh = gs.build_bvh(g)
-    packed = gs.render_views(bvh, g, cams, None, seed=3, spp=4)
+    packed = gs.render_views(bvh, g, cams, None, seed=3, spp=spp)
     views = gs.split_views(packed, cams)
     for cam, img in zip(cams, views):
-        ref = gs.trace_stochastic(bvh, g, cam, seed=3, spp=4)
+        ref = gs.trace_stochastic(bvh, g, cam, seed=3, spp=spp)
         assert torch.equal(img, ref)
     bvh.sync_status()
     bvh.free()
