@@ -54,10 +54,12 @@ def parse():
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--n-hits", type=int, default=1, help="N of the profiling case")
     ap.add_argument("--case-spp", type=int, default=1, help="spp of the profiling case")
-    ap.add_argument("--workload", choices=["shell-1m", "precision-3m", "wavefront-16v"],
+    ap.add_argument("--workload", choices=["shell-1m", "precision-3m", "wavefront-16v",
+                                           "backward-1m"],
                     default="shell-1m",
                     help="precision-3m: 3M Gaussians, FP16/BF16 SH, 8-bit 4-wide boxes; "
-                         "wavefront-16v: 16 views, ground, 4 lights, one bounce")
+                         "wavefront-16v: 16 views, ground, 4 lights, one bounce; "
+                         "backward-1m: gradients of the 1080p view")
     return ap.parse_args()
 
 
@@ -131,6 +133,61 @@ def run_wavefront(args):
             "max_abs_vs_fp32": float(np.abs(img - base).max())}
         del g
         torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
+def run_backward(args):
+    """Gradient form: the 1M shell and the 1080p view; one step = hierarchy
+    rebuild + the stochastic trace + gs_trace_backward of a seeded dLoss/dpixel
+    (gradient buffers zeroed inside the step), at N=1 spp=16 and N=4 spp=4.
+    Metric: gradient rays per second (pixels x spp / step time); each
+    gradient ray re-runs its forward traversal and enumerates the Gaussians
+    in front of its hit."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_06598_gb300 as gs
+    import scenes
+    cloud = scenes.shell_cloud(0, M=M_GAUSS)
+    g = gs.Gaussians.from_cloud(cloud)
+    cam = gs.Camera(W_IMG, H_IMG)
+    bvh = gs.build_bvh(g)
+    rng = np.random.default_rng(3)
+    d_rgb = torch.from_numpy(rng.normal(size=(H_IMG, W_IMG, 3)).astype(np.float32) * 1e-3).cuda()
+    grads = {"means": torch.zeros_like(g.means), "log_scales": torch.zeros_like(g.log_scales),
+             "quats": torch.zeros_like(g.quats), "opacity_logits": torch.zeros_like(g.opacity_logits),
+             "sh": torch.zeros(g.sh.shape, dtype=torch.float32, device="cuda")}
+    rgb = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = {"metric": "gradient form: Mrays/s of trace + backward at 1M Gaussians 1080p",
+           "workload": "shell-1M-1080p-backward", "unit": "Mrays/s", "forms": {}}
+    for n_hits, spp in ((1, 16), (4, 4)):
+        def step():
+            for t in grads.values():
+                t.zero_()
+            bvh.rebuild(g)
+            gs.trace_stochastic(bvh, g, cam, seed=0, spp=spp, n_hits=n_hits, out=rgb)
+            gs.trace_backward(bvh, g, cam, d_rgb, seed=0, spp=spp, n_hits=n_hits, grads=grads)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        times = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step()
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        bvh.sync_status()
+        ms = float(np.mean(times))
+        out["forms"]["N%d-spp%d" % (n_hits, spp)] = {
+            "ms_per_step": ms, "mrays_per_s": W_IMG * H_IMG * spp / (ms * 1e-3) / 1e6,
+            "msamples_per_s": W_IMG * H_IMG * spp * n_hits / (ms * 1e-3) / 1e6,
+            "grad_norm_means": float(grads["means"].norm()),
+            "grad_norm_sh": float(grads["sh"].norm())}
+    bvh.free()
     print(json.dumps(out), flush=True)
 
 
@@ -370,6 +427,9 @@ def main():
         return
     if args.workload == "wavefront-16v":
         run_wavefront(args)
+        return
+    if args.workload == "backward-1m":
+        run_backward(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -14,8 +14,12 @@
 // Nothing is stored between the forward and backward passes: each pass
 // re-runs the forward traversal with the same keys (identical winners),
 // then a second traversal clipped at the winners' depths enumerates the
-// Gaussians in front of them. Gradients are accumulated with atomics,
-// reduced across the warp first for the warp's shared leaf.
+// Gaussians in front of them. Gradients are accumulated with atomics: in
+// the per-lane form reduced across the warp for the warp's shared leaf; in
+// the grouped form (8 or more lanes on one pixel, the wide copy of that
+// width) the chain rule runs once per Gaussian and group on the lanes'
+// summed weights, and lanes whose slot holds the same Gaussian add its
+// colour gradient once.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -258,10 +262,136 @@ __device__ void enumerate_packet(const TraceArgs &a, const Ray<N> &r, const floa
     }
 }
 
-template <int N>
-__global__ void __launch_bounds__(kThreads) k_backward(const TraceArgs a) {
+// Grouped enumeration (groups of L = 2^LG lanes sharing one ray, the
+// W-wide copy with W = L): the same leaves as enumerate_packet for each
+// lane, visited once per group. The lane holding a hit leaf evaluates the
+// candidate and its colour; every lane adds its own samples' weight
+// sum_k g . (c_i - c_k) over the slots the candidate is in front of; the
+// group's sum goes back to that lane, which chains it through alpha and
+// adds the gradients once for the group.
+template <int N, int LG>
+__device__ void enumerate_group(const TraceArgs &a, const Ray<N> &r, const float ck[N][3],
+                                const float g[3], const float Y[16], uint32_t *s_ref, float *s_t,
+                                uint32_t &err) {
+    constexpr int L = 1 << LG;
+    constexpr int kCap = kGroupPool >> (5 - LG);
+    constexpr uint32_t kLaneBits = L == 32 ? 0xffffffffu : ((1u << (L & 31)) - 1u);
+    const int lane = threadIdx.x & 31;
+    const int base = lane & ~(L - 1);
+    const int sub = lane & (L - 1);
+    const uint32_t gmask = kLaneBits << base;
+    float G = r.t_far >= a.t_min ? r.t_far : -INFINITY;
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) G = fmaxf(G, __shfl_xor_sync(gmask, G, o));
+    if (!(G >= a.t_min)) return;
+    int sp = 0;
+    uint32_t node = (__ldg(a.gcnt) - 1u) << kWideCountShift;
+    uint32_t steps = 0;
+    for (;;) {
+        if (++steps > a.step_limit) {
+            err |= kErrSteps;
+            break;
+        }
+        const int n_child = (int)((node >> kWideCountShift) & 31u) + 1;
+        uint32_t ref = kEmpty;
+        float te = INFINITY;
+        bool hit = false;
+        if (sub < n_child) {
+            const float4 *cp =
+                reinterpret_cast<const float4 *>(a.grec + (node & kWideOffsetMask) + sub);
+            const float4 q0 = __ldg(cp), q1 = __ldg(cp + 1);
+            const float bx[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
+            ref = __float_as_uint(q1.z);
+            hit = slab(bx, r.inv, r.oinv, a.t_min, G, te);
+        }
+        const bool leaf = (ref & kLeafBit) != 0u;
+        if ((__ballot_sync(gmask, hit && leaf) >> base) & kLaneBits) {
+            Cand c;
+            float ci[3] = {0.0f, 0.0f, 0.0f};
+            bool ok = false;
+            if (hit && leaf) {
+                c = eval_cand(a, r.o, r.d, ref & ~kLeafBit);
+                ok = c.valid;
+                if (ok) sh_colour(a, c.gid, Y, ci);
+            }
+            float my_coef = 0.0f;
+            const bool live = r.t_far >= a.t_min;  // lanes past the last pass add nothing
+            for (uint32_t cm = (__ballot_sync(gmask, ok) >> base) & kLaneBits; cm; cm &= cm - 1u) {
+                const int src = base + __ffs(cm) - 1;
+                const float tc = __shfl_sync(gmask, c.tc, src);
+                const float tau = __shfl_sync(gmask, c.tau, src);
+                const uint32_t gid = __shfl_sync(gmask, c.gid, src);
+                float cc[3];
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) cc[ch] = __shfl_sync(gmask, ci[ch], src);
+                float coef = 0.0f;
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    if (!live || !lex_closer(tc, tau, gid, r.slot[k])) continue;
+                    coef += g[0] * (cc[0] - ck[k][0]) + g[1] * (cc[1] - ck[k][1]) +
+                            g[2] * (cc[2] - ck[k][2]);
+                }
+#pragma unroll
+                for (int o = 1; o < L; o <<= 1) coef += __shfl_xor_sync(gmask, coef, o);
+                if (lane == src) my_coef = coef;
+            }
+            if (ok && my_coef != 0.0f) {
+                // a rejected hit has alpha <= xi < 1
+                const float w = my_coef / (1.0f - c.alpha);
+                float d[11];
+                grad_alpha(a, c, d);
+                const int64_t gg = c.gid;
+                for (int k = 0; k < 3; ++k) {
+                    atomicAdd(a.g_means + 3 * gg + k, d[k] * w);
+                    atomicAdd(a.g_log_scales + 3 * gg + k, d[3 + k] * w);
+                }
+                for (int k = 0; k < 4; ++k) atomicAdd(a.g_quats + 4 * gg + k, d[6 + k] * w);
+                atomicAdd(a.g_logits + gg, d[10] * w);
+            }
+        }
+        const bool inner = hit && !leaf;
+        const uint32_t im = (__ballot_sync(gmask, inner) >> base) & kLaneBits;
+        if (im) {
+            const uint32_t key = __reduce_min_sync(
+                gmask, inner ? ((__float_as_uint(fmaxf(te, 0.0f)) & ~31u) | (uint32_t)sub)
+                             : 0xffffffffu);
+            const int nj = (int)(key & 31u);
+            const uint32_t next = __shfl_sync(gmask, ref, base + nj);
+            const uint32_t others = im & ~(1u << nj);
+            const int npush = __popc(others);
+            if (sp + npush > kCap) {
+                err |= kErrStack;
+                break;
+            }
+            __syncwarp(gmask);
+            if (inner && sub != nj) {
+                const int pos = sp + __popc(others & ((1u << sub) - 1u));
+                s_ref[pos] = ref;
+                s_t[pos] = te;
+            }
+            sp += npush;
+            __syncwarp(gmask);
+            node = next;
+            continue;
+        }
+        if (sp == 0) break;
+        --sp;  // no clip changes here: every pushed node is still needed
+        node = s_ref[sp];
+    }
+}
+
+// LG: log2 of the lanes per pixel when the grouped traversals are used, else
+// 0. The grouped form is latency-bound and built for eight resident blocks
+// per SM; the per-lane form for three.
+template <int N, int LG>
+__global__ void __launch_bounds__(kThreads, LG >= 3 ? kGroupMinBlocks : 3) k_backward(const TraceArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;
+    __shared__ uint32_t s_ref[LG >= 3 ? kThreads / 32 : 1][LG >= 3 ? kGroupPool : 1];
+    __shared__ float s_t[LG >= 3 ? kThreads / 32 : 1][LG >= 3 ? kGroupPool : 1];
+    const int grp_off = LG >= 3 ? (lane >> LG) * (kGroupPool >> (5 - (LG >= 3 ? LG : 5))) : 0;
+    uint32_t *grp_ref = s_ref[LG >= 3 ? threadIdx.x >> 5 : 0] + grp_off;
+    float *grp_t = s_t[LG >= 3 ? threadIdx.x >> 5 : 0] + grp_off;
     // pixels x samples per warp as in the forward trace
     const int lg = a.lpp_log2, L = 1 << lg;
     const int tw_lg = tile_w_log2(lg), th_lg = 5 - lg - tw_lg;
@@ -310,20 +440,35 @@ __global__ void __launch_bounds__(kThreads) k_backward(const TraceArgs a) {
             if (!live) r.t_far = -INFINITY;
             if (a.n_nodes == 0) continue;
             // 1) the forward traversal: same keys, same winners
-            traverse_packet<N, false>(a, r, pass, stack, stack_t, err, cnt);
+            if constexpr (LG >= 3)
+                traverse_group<N, false, LG>(a, r, pass, grp_ref, grp_t, err, cnt);
+            else
+                traverse_packet<N, false>(a, r, pass, stack, stack_t, err, cnt);
             // 2) colours of the winners; dLoss/dk of the selected Gaussians
             float ck[N][3];
 #pragma unroll
             for (int k = 0; k < N; ++k) {
-                if (live && r.slot[k].gid != 0xffffffffu) {
+                const uint32_t wid = live ? r.slot[k].gid : 0xffffffffu;
+                float mult = 1.0f;
+                bool leader = true;
+                if constexpr (LG >= 3) {
+                    // lanes of a pixel share g and Y: one lane adds for all
+                    // lanes whose slot k holds the same Gaussian
+                    constexpr uint32_t kBits = LG == 5 ? 0xffffffffu : ((1u << ((1 << LG) & 31)) - 1u);
+                    const uint32_t gm = kBits << (lane & ~((1 << LG) - 1));
+                    const uint32_t same = __match_any_sync(gm, wid);
+                    mult = (float)__popc(same);
+                    leader = (__ffs(same) - 1) == lane;
+                }
+                if (wid != 0xffffffffu) {
                     float raw[3];
-                    sh_colour_raw(a, r.slot[k].gid, Y, raw);
-                    const int64_t base = (int64_t)r.slot[k].gid * K * 3;
+                    sh_colour_raw(a, wid, Y, raw);
+                    const int64_t base = (int64_t)wid * K * 3;
                     for (int ch = 0; ch < 3; ++ch) {
                         ck[k][ch] = fmaxf(raw[ch], 0.0f);
-                        if (raw[ch] > 0.0f && g[ch] != 0.0f)
+                        if (leader && raw[ch] > 0.0f && g[ch] != 0.0f)
                             for (int i = 0; i < K; ++i)
-                                atomicAdd(a.g_sh + base + 3 * i + ch, g[ch] * Y[i]);
+                                atomicAdd(a.g_sh + base + 3 * i + ch, mult * g[ch] * Y[i]);
                     }
                 } else {
                     for (int ch = 0; ch < 3; ++ch) ck[k][ch] = a.bg[ch];
@@ -332,19 +477,23 @@ __global__ void __launch_bounds__(kThreads) k_backward(const TraceArgs a) {
             // 3) every Gaussian in front of a winner
             update_clip(r, a.t_max);
             if (!live) r.t_far = -INFINITY;
-            enumerate_packet<N>(a, r, ck, g, Y, stack, stack_t, err);
+            if constexpr (LG >= 3)
+                enumerate_group<N, LG>(a, r, ck, g, Y, grp_ref, grp_t, err);
+            else
+                enumerate_packet<N>(a, r, ck, g, Y, stack, stack_t, err);
             __syncwarp();
         }
     }
     if (err) atomicOr(a.status, err);
 }
 
-template <int N>
-gs_status launch_backward_n(const TraceArgs &a, cudaStream_t s) {
+template <int N, int LG>
+gs_status launch_backward_nl(const TraceArgs &a, cudaStream_t s) {
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_backward<N>, kThreads, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_backward<N, LG>, kThreads, 0);
     if (e != cudaSuccess) return cuda_fail(e, "backward launch setup");
     const int tw_lg = tile_w_log2(a.lpp_log2), th_lg = 5 - a.lpp_log2 - tw_lg;
     const uint32_t tiles = (uint32_t)(((a.width + (1 << tw_lg) - 1) >> tw_lg) *
@@ -354,8 +503,22 @@ gs_status launch_backward_n(const TraceArgs &a, cudaStream_t s) {
     if (blocks > max_blocks) blocks = max_blocks;
     if ((e = cudaMemsetAsync(a.work, 0, sizeof(uint32_t), s)) != cudaSuccess)
         return cuda_fail(e, "reset work counter");
-    k_backward<N><<<blocks, kThreads, 0, s>>>(a);
+    k_backward<N, LG><<<blocks, kThreads, 0, s>>>(a);
     return GS_OK;
+}
+
+// Groups of 8 or more lanes on one pixel use the wide copy of their width.
+template <int N>
+gs_status launch_backward_n(const TraceArgs &a, cudaStream_t s) {
+    if (a.grec != nullptr) {
+        switch (a.lpp_log2) {
+            case 5: return launch_backward_nl<N, 5>(a, s);
+            case 4: return launch_backward_nl<N, 4>(a, s);
+            case 3: return launch_backward_nl<N, 3>(a, s);
+            default: break;
+        }
+    }
+    return launch_backward_nl<N, 0>(a, s);
 }
 
 }  // namespace
@@ -392,6 +555,10 @@ gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinho
     a.status = b->status;
     a.work = b->status + 1;
     a.lpp_log2 = lanes_per_pixel_log2(p->spp);
+    if (b->node_depth && a.lpp_log2 >= 3) {
+        a.grec = b->group[a.lpp_log2 - 3].rec;
+        a.gcnt = b->group[a.lpp_log2 - 3].cnt;
+    }
     a.d_rgb = d_rgb;
     a.log_scales = g->log_scales;
     a.quats = g->quats;

@@ -47,7 +47,8 @@ def _gpu_grads(gs, cloud, cam, d_rgb, **opts):
     return {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
 
 
-@pytest.mark.parametrize("spp,n_hits", [(4, 1), (2, 4), (3, 2), (40, 1)])
+# spp >= 8 runs the grouped traversals (8, 16 and 32 lanes on one pixel)
+@pytest.mark.parametrize("spp,n_hits", [(4, 1), (2, 4), (3, 2), (40, 1), (16, 1), (8, 2)])
 def test_estimator_parity(gs, spp, n_hits):
     cloud = _cluster()
     cam = scenes.Pinhole(width=16, height=12, fov_y_deg=9.0)
@@ -137,3 +138,19 @@ def test_autograd_and_fit(gs):
     assert losses[0] > 1.5 * floor
     # most of the excess over the noise floor is gone
     assert np.mean(losses[-5:]) - floor < 0.3 * (losses[0] - floor), (floor, losses)
+
+
+def test_grouped_and_packet_gradients_agree(gs):
+    """Samples 0..15 by 16 lanes on one pixel (grouped traversals) and by 2
+    lanes x 8 slots (per-lane packets): the same per-sample hits, so the same
+    gradients up to the order of the float sums."""
+    cloud = scenes.shell_cloud(8, M=20000)
+    cam = scenes.default_camera(48, 36)
+    rng = np.random.default_rng(5)
+    d_rgb = rng.normal(size=(cam.width * cam.height, 3))
+    a = _gpu_grads(gs, cloud, cam, d_rgb, seed=2, spp=16, n_hits=1)
+    b = _gpu_grads(gs, cloud, cam, d_rgb, seed=2, spp=2, n_hits=8)
+    for k in KEYS:
+        scale = np.abs(b[k]).max()
+        assert scale > 0, k
+        assert np.abs(a[k] - b[k]).max() <= 1e-5 * scale, k
