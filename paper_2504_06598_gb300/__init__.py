@@ -357,10 +357,12 @@ class StochasticRender(torch.autograd.Function):
     def forward(ctx, means, log_scales, quats, opacity_logits, sh, sh_degree, cam, options):
         options = dict(options)
         shared = options.pop("bvh", None)
+        rebuild = options.pop("rebuild", True)
         g = Gaussians(means.detach(), log_scales.detach(), quats.detach(),
                       opacity_logits.detach(), sh.detach(), sh_degree)
         if shared is not None:
-            shared.rebuild(g)  # reuse the caller's handle: no allocation
+            if rebuild:
+                shared.rebuild(g)  # reuse the caller's handle: no allocation
             bvh = shared
         else:
             bvh = build_bvh(g)
@@ -384,7 +386,9 @@ def render_differentiable(means, log_scales, quats, opacity_logits, sh, sh_degre
 
     ``bvh=`` (optional) is a handle to rebuild in place instead of building
     a new one per call; its backward must run before the next forward that
-    uses the same handle."""
+    uses the same handle. ``rebuild=False`` uses that handle as it is: the
+    caller has already rebuilt it from these same parameters (several views
+    of one parameter state share one rebuild)."""
     return StochasticRender.apply(means, log_scales, quats, opacity_logits, sh, sh_degree, cam,
                                   options)
 

@@ -95,10 +95,12 @@ def fit(steps=200, spp=4, n_hits=1, lr=None, M=500_000, views=16, res=800, seed=
         t0 = time.perf_counter()
         opt.zero_grad()
         total = 0.0
+        # one hierarchy rebuild per parameter state, shared by all views
+        bvh.rebuild(gs.Gaussians(*(params[k].detach() for k in KEYS), cloud.sh_degree))
         for v, cam in enumerate(cams):
             img = gs.render_differentiable(params["means"], params["log_scales"], params["quats"],
                                            params["opacity_logits"], params["sh"],
-                                           cloud.sh_degree, cam, bvh=bvh,
+                                           cloud.sh_degree, cam, bvh=bvh, rebuild=False,
                                            seed=step * len(cams) + v, spp=spp, n_hits=n_hits)
             loss = ((img - targets[v]) ** 2).mean()
             loss.backward()
