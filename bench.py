@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-pixels", type=int, default=512,
                     help="pixels per step of the reference (oracle) arm")
-    ap.add_argument("--case", choices=["trace-1080p"], default=None,
+    ap.add_argument("--case", choices=["trace-1080p", "wavefront-4v", "backward-1080p"], default=None,
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--n-hits", type=int, default=1, help="N of the profiling case")
     ap.add_argument("--case-spp", type=int, default=1, help="spp of the profiling case")
@@ -260,9 +260,10 @@ def run_precision(args):
 
 
 def run_case(args):
-    """Profiling case: the 1M-Gaussian shell, the 1920x1080 view, spp=1
-    (or --case-spp), traced twice (warm-up launch, then the launch to
-    capture)."""
+    """Profiling cases on the 1M-Gaussian shell, each launched twice (warm-up
+    launch, then the launch to capture), spp from --case-spp (default 1):
+    trace-1080p (the 1920x1080 view), backward-1080p (trace + gradients of
+    that view), wavefront-4v (the batched form on four 480x270 views)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -272,12 +273,26 @@ def run_case(args):
     g = gs.Gaussians.from_cloud(cloud)
     bvh = gs.build_bvh(g)
     cam = gs.Camera(W_IMG, H_IMG)
-    for _ in range(2):
-        gs.trace_stochastic(bvh, g, cam, seed=0, spp=args.case_spp, n_hits=args.n_hits)
+    if args.case == "trace-1080p":
+        for _ in range(2):
+            gs.trace_stochastic(bvh, g, cam, seed=0, spp=args.case_spp, n_hits=args.n_hits)
+    elif args.case == "backward-1080p":
+        # the gradient launch of the spp given (trace first, as a user would)
+        rng = np.random.default_rng(3)
+        d_rgb = torch.from_numpy(rng.normal(size=(H_IMG, W_IMG, 3)).astype(np.float32)).cuda()
+        for _ in range(2):
+            gs.trace_stochastic(bvh, g, cam, seed=0, spp=args.case_spp, n_hits=args.n_hits)
+            gs.trace_backward(bvh, g, cam, d_rgb, seed=0, spp=args.case_spp, n_hits=args.n_hits)
+    else:
+        # the batched form on four 480x270 views with ground, lights, bounce
+        cams = scenes.wavefront_views(4, seed=0, fixed_res=(480, 270))
+        ex = scenes.ground_and_lights(4, seed=0)
+        for _ in range(2):
+            gs.render_views(bvh, g, cams, ex, seed=0, spp=args.case_spp)
     bvh.sync_status()
     torch.cuda.synchronize()
     bvh.free()
-    print("case trace-1080p done")
+    print("case %s done" % args.case)
 
 
 def dist_env():

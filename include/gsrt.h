@@ -362,9 +362,23 @@ typedef struct gs_launch_options {
     int32_t reserved[6];
 } gs_launch_options;
 
-/* Render n_views pinhole views (1..32, uneven sizes allowed) in one
- * persistent launch: warps take 8x4 tiles from a queue over all views and
- * trace each tile's camera, shadow and bounce rays as warp packets.
+/* Render n_views pinhole views (1..32, uneven sizes allowed). Warps take
+ * pixel tiles from one queue over all views, the lanes of a pixel taking
+ * its samples as in gs_trace_stochastic; camera and shadow rays are one ray
+ * per pixel (grouped traversal of the wide copies on binary handles with
+ * 8 or more lanes per pixel, warp packets otherwise). When the ground and
+ * the bounce are on (and the views hold fewer than 2^24 - 1 pixels, spp <=
+ * 1024) the bounce rays are deferred: each sample slot gets a sort code
+ * (direction bin, then ground cell), the codes are radix-sorted, and a
+ * second pass traces the bounce rays as warp packets in that order and
+ * adds each pixel's bounce radiance in sample order; otherwise each lane
+ * traces its bounce ray alone (binary nodes) or in a warp packet. The
+ * deferred pass needs 28 bytes of device scratch per sample slot (total
+ * pixels x spp), held by the handle and grown on first use (a synchronous
+ * allocation; refused with GS_ERR_INVALID_ARG while `stream` is capturing
+ * a graph: gs_graph_capture_views reserves it before capturing). The call
+ * therefore modifies the handle's scratch, and calls on one handle must not
+ * overlap on the GPU.
  *   bvh, g      as for gs_trace_stochastic (any node format)
  *   cams        host array [n_views]; ray ids must not overlap
  *   ex          host struct (above); NULL = no ground, lights or bounce
@@ -374,7 +388,8 @@ typedef struct gs_launch_options {
  *               at pixel sum_{u<v} width_u * height_u
  *   counters    optional device uint64[4] incremented by the launch:
  *               {camera rays, shadow rays, bounce rays, node fetches by
- *               warps}
+ *               warps (child records fetched by groups in the grouped
+ *               traversal)}
  *   samples_out optional device int32[spp][total pixels][3], per sample:
  *               camera hit (Gaussian id, -2 ground, -1 nothing), bounce hit
  *               (Gaussian id or -1), bit l set when light l was visible
@@ -388,8 +403,9 @@ gs_status gs_render_views(const gs_bvh *bvh, const gs_gaussians *g, const gs_pin
  * (parameters re-read from the same device arrays at every replay), then
  * the gs_render_views launch, recorded once as a CUDA graph and replayed
  * with gs_graph_launch. Arguments as for gs_render_views; `stream` must be
- * a non-default stream (the legacy default stream cannot be captured).
- * Every replay renders the same rays with the same keys. */
+ * a non-default stream (the legacy default stream cannot be captured). The
+ * deferred bounce's scratch is reserved before the capture starts. Every
+ * replay renders the same rays with the same keys. */
 typedef struct gs_graph gs_graph;
 
 gs_status gs_graph_capture_views(gs_bvh *bvh, const gs_gaussians *g, int32_t rebuild,

@@ -90,6 +90,9 @@ static void release(gs_bvh *b) {
         if (t.cnt) cudaFree(t.cnt);
         if (t.off) cudaFree(t.off);
     }
+    void *wave[] = {b->wave_codes[0], b->wave_codes[1], b->wave_bounce, b->wave_hist, b->wave_scan};
+    for (void *p : wave)
+        if (p) cudaFree(p);
     free(b);
 }
 
@@ -460,6 +463,14 @@ gs_status gs_graph_capture_views(gs_bvh *b, const gs_gaussians *g, int32_t rebui
         if (!b || g->M > b->capacity) return fail(GS_ERR_INVALID_ARG, "rebuild exceeds capacity");
     }
     cudaStream_t s = (cudaStream_t)stream;
+    // the deferred bounce's scratch cannot be allocated inside a capture
+    if (b && cams && n_views >= 1 && n_views <= 32 && p) {
+        const int64_t slots = wave_slots(cams, n_views, ex, p);
+        if (slots > 0) {
+            gs_status st = reserve_wave_scratch(b, slots, s);
+            if (st != GS_OK) return st;
+        }
+    }
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "begin capture");
     gs_status st = GS_OK;

@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kSortThreads)
         int64_t i = tile0 + r * kSortThreads + tid;
         bool valid = i < n;
         unsigned long long key = valid ? kin[i] : 0ull;
-        uint32_t val = valid ? vin[i] : 0u;
+        uint32_t val = (valid && vin) ? vin[i] : 0u;
         uint32_t digit = valid ? ((uint32_t)(key >> shift) & 255u) : (256u + lane);
         uint32_t peers = __match_any_sync(0xffffffffu, digit);
         uint32_t rank = __popc(peers & ((1u << lane) - 1u));
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(kSortThreads)
         if (valid) {
             uint32_t pos = pref[warp][digit] + rank;
             kout[pos] = key;
-            vout[pos] = val;
+            if (vout) vout[pos] = val;
         }
     }
 }
@@ -646,6 +646,20 @@ inline unsigned grid_for(int64_t n, int threads) {
 }  // namespace
 
 int64_t radix_tiles(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+
+int sort_keys64(unsigned long long *keys[2], int64_t n, int lo_bit, uint32_t *hist,
+                uint32_t *scan_tmp, cudaStream_t s) {
+    const int64_t tiles = radix_tiles(n);
+    int cur = 0;
+    for (int shift = lo_bit; shift < 64; shift += 8) {
+        k_radix_hist<<<(unsigned)tiles, kSortThreads, 0, s>>>(n, keys[cur], shift, hist, tiles);
+        scan_exclusive(hist, 256 * tiles, scan_tmp, s);
+        k_radix_scatter<<<(unsigned)tiles, kSortThreads, 0, s>>>(n, keys[cur], nullptr, keys[1 - cur],
+                                                                 nullptr, shift, hist, tiles);
+        cur = 1 - cur;
+    }
+    return cur;
+}
 
 int64_t scan_tmp_entries(int64_t n) { return (n + kScanItems - 1) / kScanItems + 1; }
 

@@ -130,6 +130,12 @@ struct gs_bvh {
     // only): W = 8, 16, 32, each at most M + (M - 1) records
     gsrt::GroupTree group[gsrt::kGroupTrees];
     uint32_t *node_depth;  // depth of every binary internal node
+    // scratch of the batched form's deferred bounce rays, grown on demand
+    int64_t wave_cap;                    // sample slots (pixels x spp) held
+    unsigned long long *wave_codes[2];   // one sort code per slot
+    float *wave_bounce;                  // [slots][3] albedo x bounce radiance
+    uint32_t *wave_hist;                 // radix histograms of the codes
+    uint32_t *wave_scan;                 // scan block sums
 };
 
 namespace gsrt {
@@ -143,6 +149,21 @@ bool is_device_ptr(const void *p);
 gs_status build_into(gs_bvh *b, const gs_gaussians *g, cudaStream_t s);
 int64_t radix_tiles(int64_t n);
 int64_t scan_tmp_entries(int64_t n);
+// Stable LSD radix sort of n 64-bit keys on bits [lo_bit, 64), 8 bits per
+// pass, ping-ponging between keys[0] and keys[1]; returns the index of the
+// buffer holding the result. hist: 256 * radix_tiles(n) entries, scan_tmp:
+// scan_tmp_entries(256 * radix_tiles(n)).
+int sort_keys64(unsigned long long *keys[2], int64_t n, int lo_bit, uint32_t *hist,
+                uint32_t *scan_tmp, cudaStream_t s);
+
+// Batched form (wavefront.cu): grows the handle's deferred-bounce scratch to
+// `slots` sample slots (synchronous allocation; refused while the stream is
+// capturing a graph).
+gs_status reserve_wave_scratch(gs_bvh *b, int64_t slots, cudaStream_t s);
+// Sample slots the batched form needs for these views and options (0 when
+// the bounce is traced inline).
+int64_t wave_slots(const gs_pinhole *cams, int n_views, const gs_scene_extras *ex,
+                   const gs_trace_params *p);
 
 // Backward (backward.cu)
 gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,

@@ -44,10 +44,12 @@ __host__ __device__ constexpr bool is_group_fmt(int f) { return f >= kFmtGroup +
 
 // Persistent kernel: each warp repeatedly takes the next tile (one atomic
 // per tile, so the tail of the launch stays balanced), then runs all passes
-// of its pixels. The cooperative form is latency-bound and is built for
-// eight resident blocks per SM (five with eight slots per lane).
+// of its pixels. The grouped form is latency-bound and is built for eight
+// resident blocks per SM (five with eight slots per lane), the per-lane
+// packet form for five (up to four slots).
 template <int N, bool COUNT, int FMT>
-__global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? (N >= 8 ? 5 : kGroupMinBlocks) : 1)
+__global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? (N >= 8 ? 5 : kGroupMinBlocks)
+                                                               : (N >= 8 ? 1 : 5))
     k_trace(const TraceArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;

@@ -51,7 +51,41 @@ struct WaveArgs {
     unsigned long long *counters;
     int32_t *samples;  // optional [spp][n_pix][3] diagnostics
     int64_t n_pix;
+    // deferred bounce: the camera pass writes one sort code per sample slot
+    // (pixel * spp + sample); the bounce pass writes albedo x radiance
+    int deferred;
+    unsigned long long *codes;
+    float *bounce_rgb;
 };
+
+// Sort code of a deferred bounce ray: 28 key bits (direction bin in an
+// octahedral 64x64 map of the upper hemisphere, then the Morton order of
+// the ground point on a 256x256 grid) above the pixel (24 bits) and the
+// sample (10 bits). Codes of samples without a bounce are all ones; a
+// bounce code is below 2^62, so on the sorted bits 32..63 it is strictly
+// below every empty code and all empty codes sort last.
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long bounce_code(const WaveArgs &w, const float p[3],
+                                                          const float d[3], int64_t gpix, int s) {
+    const float l1 = fabsf(d[0]) + fabsf(d[1]) + fabsf(d[2]);
+    const float u = d[0] / l1, v = d[2] / l1;
+    const uint32_t qu = (uint32_t)min(63, max(0, (int)((u + 1.0f) * 32.0f)));
+    const uint32_t qv = (uint32_t)min(63, max(0, (int)((v + 1.0f) * 32.0f)));
+    const float inv = w.ground_half > 0.0f ? 1.0f / w.ground_half : 0.0f;
+    const uint32_t qx = (uint32_t)min(255, max(0, (int)((p[0] * inv + 1.0f) * 128.0f)));
+    const uint32_t qz = (uint32_t)min(255, max(0, (int)((p[2] * inv + 1.0f) * 128.0f)));
+    const uint32_t key = (((qu << 6) | qv) << 16) | spread10(qx) | (spread10(qz) << 1);
+    return ((unsigned long long)key << 34) | ((unsigned long long)gpix << 10) |
+           (unsigned long long)s;
+}
 
 // Bounce direction: cosine-weighted about +y, normalise(n + u) with u
 // uniform on the unit sphere by rejection from Philox lanes.
@@ -235,8 +269,25 @@ __global__ void k_render_views(const WaveArgs w) {
                         c[i] = fmaf(w.albedo_over_pi[i] * w.light_int[l][i], k, c[i]);
                 }
             }
-            // one diffuse bounce
-            if (w.bounce) {
+            // one diffuse bounce: deferred to the sorted bounce pass, or
+            // traced here
+            if (w.bounce && w.deferred) {
+                if (live) {
+                    const int64_t gpix = vw.pix_begin + lpix;
+                    const int64_t slot = gpix * a.spp + s;
+                    unsigned long long code = ~0ull;
+                    if (on_ground) {
+                        float db[3] = {0.0f, 1.0f, 0.0f};
+                        bounce_dir(a, ray_id, (uint32_t)s, db);
+                        code = bounce_code(w, p, db, gpix, s);
+                        ++n_bounce;
+                    }
+                    w.codes[slot] = code;
+                    w.bounce_rgb[3 * slot] = 0.0f;
+                    w.bounce_rgb[3 * slot + 1] = 0.0f;
+                    w.bounce_rgb[3 * slot + 2] = 0.0f;
+                }
+            } else if (w.bounce) {
                 float db[3] = {0.0f, 1.0f, 0.0f};
                 if (on_ground) bounce_dir(a, ray_id, (uint32_t)s, db);
                 const bool need = on_ground;
@@ -301,6 +352,126 @@ __global__ void k_render_views(const WaveArgs w) {
     }
 }
 
+// Deferred bounce pass: warps take 32 consecutive sorted codes, so a packet
+// holds bounce rays of nearby directions from nearby ground points (the
+// path tracer's wavefront regrouping of secondary rays). Each
+// lane rebuilds its sample's ground point and bounce direction with the
+// camera pass's arithmetic, traces, shades, and writes albedo x radiance to
+// the sample's slot. The first all-empty tile ends the pass (empty codes
+// sort last).
+template <int FMT, int STACK, bool COUNT>
+__global__ void k_bounce(const WaveArgs w, const unsigned long long *__restrict__ codes,
+                         int64_t n_slots) {
+    const TraceArgs &a = w.t;
+    const int lane = threadIdx.x & 31;
+    const uint32_t kAll = 0xffffffffu;
+    uint32_t stack[STACK];
+    float stack_t[STACK];
+    uint32_t err = 0;
+    Counts cnt;
+    for (;;) {
+        uint32_t tile = 0;
+        if (lane == 0) tile = atomicAdd(a.work, 1u);
+        tile = __shfl_sync(kAll, tile, 0);
+        if ((int64_t)tile * 32 >= n_slots) break;
+        const int64_t i = (int64_t)tile * 32 + lane;
+        const unsigned long long code = i < n_slots ? codes[i] : ~0ull;
+        const bool valid = code != ~0ull;
+        if (!__any_sync(kAll, valid)) break;
+        const int64_t gpix = valid ? (int64_t)((code >> 10) & 0xffffffull) : 0;
+        const int s = valid ? (int)(code & 1023ull) : 0;
+        int v = 0;
+        while (v + 1 < w.n_views && w.views[v + 1].pix_begin <= gpix) ++v;
+        const ViewDesc &vw = w.views[v];
+        const int64_t lpix = gpix - vw.pix_begin;
+        const int x = (int)(lpix % vw.width), y = (int)(lpix / vw.width);
+        const uint32_t ray_id = vw.ray_id_offset + (uint32_t)lpix;
+        float d0[3];
+        camera_ray_view(vw.eye, vw.look_at, vw.up, vw.tan_half, vw.width, vw.height, x, y, d0);
+        float p[3] = {0.0f, w.ground_y, 0.0f};
+        float db[3] = {0.0f, 1.0f, 0.0f};
+        if (valid) {
+            const float tq = __fdiv_rn(__fsub_rn(w.ground_y, vw.eye[1]), d0[1]);
+            p[0] = __fadd_rn(vw.eye[0], __fmul_rn(tq, d0[0]));
+            p[2] = __fadd_rn(vw.eye[2], __fmul_rn(tq, d0[2]));
+            bounce_dir(a, ray_id, (uint32_t)s, db);
+        }
+        Ray<1> br;
+        set_ray(br, p, db);
+        br.ray_id = ray_id;
+        br.stream_tag = kTagBounce;
+        br.t_min = w.eps;
+        br.t_max = INFINITY;
+        br.any_hit = false;
+        reset_slots(br);
+        update_clip(br, br.t_max);
+        if (!valid) br.t_far = -INFINITY;
+        trace_packet<FMT, COUNT>(a, br, s, stack, stack_t, err, cnt);
+        if (valid) {
+            float lb[3] = {a.bg[0], a.bg[1], a.bg[2]};
+            if (br.slot[0].gid != 0xffffffffu) {
+                float Yb[16];
+                sh_basis(a.sh_degree, db, Yb);
+                sh_colour(a, br.slot[0].gid, Yb, lb);
+                if (w.samples)
+                    w.samples[((int64_t)s * w.n_pix + gpix) * 3 + 1] = (int32_t)br.slot[0].gid;
+            }
+            const int64_t slot = gpix * a.spp + s;
+            for (int c = 0; c < 3; ++c) w.bounce_rgb[3 * slot + c] = w.albedo[c] * lb[c];
+        }
+        __syncwarp();
+    }
+    if (err) atomicOr(a.status, err);
+    if (COUNT) atomicAdd(w.counters + 3, cnt.node_fetch);
+}
+
+// Adds each pixel's bounce radiance, in sample order, to its mean.
+__global__ void k_combine(const WaveArgs w) {
+    const int64_t px = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (px >= w.n_pix) return;
+    const TraceArgs &a = w.t;
+    float sum[3] = {0.0f, 0.0f, 0.0f};
+    const float *b = w.bounce_rgb + 3 * px * a.spp;
+    for (int s = 0; s < a.spp; ++s)
+        for (int c = 0; c < 3; ++c) sum[c] += b[3 * s + c];
+    const float inv_n = 1.0f / (float)a.spp;
+    for (int c = 0; c < 3; ++c) a.rgb[3 * px + c] = fmaf(sum[c], inv_n, a.rgb[3 * px + c]);
+}
+
+template <int FMT, int STACK, bool COUNT>
+gs_status launch_bounce(const WaveArgs &w, const unsigned long long *codes, int64_t n_slots,
+                        int threads, cudaStream_t s) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bounce<FMT, STACK, COUNT>,
+                                                          threads, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "bounce launch setup");
+    const int64_t tiles = (n_slots + 31) / 32;
+    const uint32_t warps_per_block = (uint32_t)threads / 32;
+    uint32_t blocks = (uint32_t)sms * (uint32_t)(per > 0 ? per : 1);
+    const int64_t max_blocks = (tiles + warps_per_block - 1) / warps_per_block;
+    if ((int64_t)blocks > max_blocks) blocks = (uint32_t)max_blocks;
+    if (blocks == 0) return GS_OK;
+    if ((e = cudaMemsetAsync(w.t.work, 0, sizeof(uint32_t), s)) != cudaSuccess)
+        return cuda_fail(e, "reset work counter");
+    k_bounce<FMT, STACK, COUNT><<<blocks, threads, 0, s>>>(w, codes, n_slots);
+    k_combine<<<(unsigned)((w.n_pix + 255) / 256), 256, 0, s>>>(w);
+    return GS_OK;
+}
+
+template <int FMT>
+gs_status launch_bounce_f(const WaveArgs &w, const unsigned long long *codes, int64_t n_slots,
+                          int threads, int stack, cudaStream_t s) {
+    const bool count = w.counters != nullptr;
+    if (stack == 48)
+        return count ? launch_bounce<FMT, 48, true>(w, codes, n_slots, threads, s)
+                     : launch_bounce<FMT, 48, false>(w, codes, n_slots, threads, s);
+    return count ? launch_bounce<FMT, 96, true>(w, codes, n_slots, threads, s)
+                 : launch_bounce<FMT, 96, false>(w, codes, n_slots, threads, s);
+}
+
 template <int FMT, int STACK, bool COUNT, int GLG>
 gs_status launch_views(const WaveArgs &w, int threads, cudaStream_t s) {
     int dev = 0, sms = 0, per = 0;
@@ -352,6 +523,47 @@ gs_status launch_views_f<GS_NODES_BINARY>(const WaveArgs &w, int threads, int st
 }
 
 }  // namespace
+
+int64_t wave_slots(const gs_pinhole *cams, int n_views, const gs_scene_extras *ex,
+                   const gs_trace_params *p) {
+    if (!ex || !ex->bounce || !ex->has_ground || p->spp < 1 || p->spp > 1024) return 0;
+    int64_t pix = 0;
+    for (int v = 0; v < n_views; ++v) pix += (int64_t)cams[v].width * cams[v].height;
+    if (pix >= (int64_t)(1 << 24) - 1) return 0;  // the code's pixel field
+    return pix * p->spp;
+}
+
+gs_status reserve_wave_scratch(gs_bvh *b, int64_t slots, cudaStream_t s) {
+    if (b->wave_cap >= slots) return GS_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return fail(GS_ERR_INVALID_ARG,
+                    "the batched form's scratch must be reserved before a graph capture");
+    void **bufs[] = {(void **)&b->wave_codes[0], (void **)&b->wave_codes[1],
+                     (void **)&b->wave_bounce, (void **)&b->wave_hist, (void **)&b->wave_scan};
+    for (void **q : bufs)
+        if (*q) {
+            cudaFree(*q);
+            *q = nullptr;
+        }
+    const int64_t tiles = radix_tiles(slots);
+    const size_t sizes[] = {(size_t)slots * 8, (size_t)slots * 8, (size_t)slots * 12,
+                            (size_t)tiles * 256 * 4, (size_t)scan_tmp_entries(256 * tiles) * 4};
+    for (int k = 0; k < 5; ++k) {
+        cudaError_t e = cudaMalloc(bufs[k], sizes[k]);
+        if (e != cudaSuccess) {
+            for (void **q : bufs)
+                if (*q) {
+                    cudaFree(*q);
+                    *q = nullptr;
+                }
+            b->wave_cap = 0;
+            return cuda_fail(e, "batched form scratch");
+        }
+    }
+    b->wave_cap = slots;
+    return GS_OK;
+}
 
 gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cams,
                               int n_views, const gs_scene_extras *ex, const gs_trace_params *p,
@@ -427,13 +639,38 @@ gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_p
     w.counters = counters;
     w.samples = samples;
     const int threads = opt && opt->block_threads ? opt->block_threads : 128;
+    // the bounce rays are sorted by direction and ground position and traced
+    // in a pass of their own; the handle holds the scratch
+    const int64_t slots = wave_slots(cams, n_views, ex, p);
     gs_status st;
+    if (slots > 0) {
+        gs_bvh *mb = const_cast<gs_bvh *>(b);
+        if ((st = reserve_wave_scratch(mb, slots, s)) != GS_OK) return st;
+        w.deferred = 1;
+        w.codes = mb->wave_codes[0];
+        w.bounce_rgb = mb->wave_bounce;
+    }
     switch (b->node_format) {
         case GS_NODES_WIDE4: st = launch_views_f<GS_NODES_WIDE4>(w, threads, stack, s); break;
         case GS_NODES_WIDE4_Q8: st = launch_views_f<GS_NODES_WIDE4_Q8>(w, threads, stack, s); break;
         default: st = launch_views_f<GS_NODES_BINARY>(w, threads, stack, s); break;
     }
     if (st != GS_OK) return st;
+    if (slots > 0) {
+        gs_bvh *mb = const_cast<gs_bvh *>(b);
+        const int cur = sort_keys64(mb->wave_codes, slots, 32, mb->wave_hist, mb->wave_scan, s);
+        const unsigned long long *sorted = mb->wave_codes[cur];
+        switch (b->node_format) {
+            case GS_NODES_WIDE4:
+                st = launch_bounce_f<GS_NODES_WIDE4>(w, sorted, slots, threads, stack, s);
+                break;
+            case GS_NODES_WIDE4_Q8:
+                st = launch_bounce_f<GS_NODES_WIDE4_Q8>(w, sorted, slots, threads, stack, s);
+                break;
+            default: st = launch_bounce_f<GS_NODES_BINARY>(w, sorted, slots, threads, stack, s); break;
+        }
+        if (st != GS_OK) return st;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "render launch");
     return GS_OK;
