@@ -207,7 +207,8 @@ def run_precision(args):
     cam = gs.Camera(W_IMG, H_IMG)
     npix = W_IMG * H_IMG
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    forms = [("fp32-binary", torch.float32, "binary"), ("fp32-wide4", torch.float32, "wide4"),
+    forms = [("fp32-binary", torch.float32, "binary"), ("fp16-binary", torch.float16, "binary"),
+             ("bf16-binary", torch.bfloat16, "binary"), ("fp32-wide4", torch.float32, "wide4"),
              ("fp16-wide4q8", torch.float16, "wide4_q8"), ("bf16-wide4q8", torch.bfloat16, "wide4_q8")]
     pix = scenes.pixel_subset(W_IMG, H_IMG, 4096)
     t0 = time.perf_counter()
@@ -585,6 +586,8 @@ def main():
                "warp_request_gbs": warp / (trace_ms * 1e-3) / 1e9,
                "peak_kind": peak_kind, "kernel": "k_trace<%d>" % n_hits,
                "alg_bytes_per_ray": per_ray,
+               # rays per second HBM could feed if every algorithmic byte came from DRAM
+               "hbm_ceiling_mrays_per_s": peak * 1e9 / per_ray / 1e6,
                "binary_nodes_per_ray": bv["nodes"] / (bv["rays"] * bv["spp"]),
                "gaussians_tested_per_ray": bv["prims"] / (bv["rays"] * bv["spp"])}
         if traffic is not None:
