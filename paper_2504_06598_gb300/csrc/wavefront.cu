@@ -150,11 +150,17 @@ __device__ __forceinline__ void trace_pixel_ray(const TraceArgs &a, Ray<1> &r, i
     else trace_packet<FMT, COUNT>(a, r, pass, stack, stack_t, err, cnt);
 }
 
+// Both passes of the batched form are latency-bound; they are built for 64
+// registers (four 256-thread or eight 128-thread blocks per SM), measured
+// faster than 80 or 105 registers at fewer blocks.
+constexpr int kWaveMaxThreads = 256;
+constexpr int kWaveMinBlocks = 4;
+
 // GLG: log2 of the lanes per pixel when the grouped traversal is used, else
 // 0. The group stacks are dynamic shared memory: per warp kGroupPool
 // references then kGroupPool entry distances.
 template <int FMT, int STACK, bool COUNT, int GLG>
-__global__ void k_render_views(const WaveArgs w) {
+__global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks) k_render_views(const WaveArgs w) {
     const TraceArgs &a = w.t;
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;
@@ -360,8 +366,8 @@ __global__ void k_render_views(const WaveArgs w) {
 // the sample's slot. The first all-empty tile ends the pass (empty codes
 // sort last).
 template <int FMT, int STACK, bool COUNT>
-__global__ void k_bounce(const WaveArgs w, const unsigned long long *__restrict__ codes,
-                         int64_t n_slots) {
+__global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks)
+    k_bounce(const WaveArgs w, const unsigned long long *__restrict__ codes, int64_t n_slots) {
     const TraceArgs &a = w.t;
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;
