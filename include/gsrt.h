@@ -170,7 +170,8 @@ typedef struct gs_bvh_info {
     int64_t M;            /* Gaussians indexed */
     int64_t n_nodes;      /* internal binary nodes (max(M-1, 1), 0 when M = 0) */
     int64_t capacity;     /* largest M a rebuild can take without allocating */
-    int64_t device_bytes; /* device memory held by the handle */
+    int64_t device_bytes; /* device memory held by the handle (including the
+                             batched form's scratch, once allocated) */
     int32_t node_bytes;   /* bytes per binary node record */
     int32_t prim_bytes;   /* bytes per Gaussian record */
     int32_t node_format;  /* GS_NODES_* the traversal uses */

@@ -132,6 +132,7 @@ struct gs_bvh {
     uint32_t *node_depth;  // depth of every binary internal node
     // scratch of the batched form's deferred bounce rays, grown on demand
     int64_t wave_cap;                    // sample slots (pixels x spp) held
+    int64_t wave_bytes;                  // device bytes of the scratch below
     unsigned long long *wave_codes[2];   // one sort code per slot
     float *wave_bounce;                  // [slots][3] albedo x bounce radiance
     uint32_t *wave_hist;                 // radix histograms of the codes

@@ -552,6 +552,9 @@ gs_status reserve_wave_scratch(gs_bvh *b, int64_t slots, cudaStream_t s) {
             cudaFree(*q);
             *q = nullptr;
         }
+    b->device_bytes -= b->wave_bytes;
+    b->wave_bytes = 0;
+    b->wave_cap = 0;
     const int64_t tiles = radix_tiles(slots);
     const size_t sizes[] = {(size_t)slots * 8, (size_t)slots * 8, (size_t)slots * 12,
                             (size_t)tiles * 256 * 4, (size_t)scan_tmp_entries(256 * tiles) * 4};
@@ -568,6 +571,8 @@ gs_status reserve_wave_scratch(gs_bvh *b, int64_t slots, cudaStream_t s) {
         }
     }
     b->wave_cap = slots;
+    for (size_t z : sizes) b->wave_bytes += (int64_t)z;
+    b->device_bytes += b->wave_bytes;
     return GS_OK;
 }
 
