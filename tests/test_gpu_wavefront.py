@@ -123,3 +123,35 @@ def test_autotuner(gs, tmp_path):
     assert len(res["trials"]) == len(autotune.FORMATS) * len(autotune.STACKS) * len(autotune.BLOCKS)
     again = autotune.autotune(g, cams, ex, spp=1, cache_path=path)
     assert again["cached"] and again["node_format"] == res["node_format"]
+
+
+def test_inline_bounce_path_and_scratch_accounting(gs):
+    """spp > 1024 keeps each bounce ray in the camera pass (the deferred,
+    sorted pass covers up to 1024 samples): per-sample outcomes still match
+    the oracle. A deferred frame grows the handle's reported device memory by
+    its scratch."""
+    cloud = scenes.shell_cloud(7, M=6000)
+    cams = scenes.wavefront_views(1, seed=3, fixed_res=(8, 6))
+    ex = scenes.ground_and_lights(4, seed=1)
+    g = gs.Gaussians.from_cloud(cloud)
+    bvh = gs.build_bvh(g)
+    before = bvh.info()["device_bytes"]
+    spp = 1025
+    rgb, smp = gs.render_views(bvh, g, cams, ex, seed=4, spp=spp, want_samples=True)
+    bvh.sync_status()
+    assert bvh.info()["device_bytes"] == before  # no scratch: traced inline
+    ref = oracle.render_scene(cloud, cams, ex, scenes.TraceSettings(seed=4, spp=spp), _items(cams))
+    diag = np.transpose(ref["diag"], (1, 0, 2))
+    smp = smp.cpu().numpy()
+    assert (diag[..., 0] == -2).mean() > 0.05
+    mism = np.any(smp != diag, axis=2)
+    assert mism.mean() <= 1e-3, (mism.sum(), np.argwhere(mism)[:5])
+    same = ~mism.any(axis=0)
+    est = ref["est"][same]
+    err = np.abs(rgb.cpu().numpy()[same] - est) - (1e-5 * np.abs(est) + 1e-6)
+    assert err.max() <= 0.0, err.max()
+    gs.render_views(bvh, g, cams, ex, seed=4, spp=16)
+    bvh.sync_status()
+    slots = cams[0].width * cams[0].height * 16
+    assert bvh.info()["device_bytes"] >= before + 28 * slots
+    bvh.free()
