@@ -311,7 +311,8 @@ __device__ void enumerate_group(const TraceArgs &a, const Ray<N> &r, const float
             bool ok = false;
             if (hit && leaf) {
                 c = eval_cand(a, r.o, r.d, ref & ~kLeafBit);
-                ok = c.valid;
+                // in front of some lane's winner only if t <= that lane's clip <= G
+                ok = c.valid && c.t <= G;
                 if (ok) sh_colour(a, c.gid, Y, ci);
             }
             float my_coef = 0.0f;

@@ -860,7 +860,10 @@ __device__ __forceinline__ void traverse_group(const TraceArgs &a, Ray<N> &r, in
                 ck1 = c.key_tc;
                 ck2 = c.key_tau;
                 cgid = c.gid;
+                // a lane takes a candidate only at t <= its own clip <= G
+                ok = ok && ct <= G;
             }
+            const float far0 = r.t_far;
             // every lane: its own draws against each candidate
             for (uint32_t cm = (__ballot_sync(gmask, ok) >> base) & kLaneBits; cm; cm &= cm - 1u) {
                 const int src = base + __ffs(cm) - 1;
@@ -873,9 +876,12 @@ __device__ __forceinline__ void traverse_group(const TraceArgs &a, Ray<N> &r, in
                 if (closer_slots<N>(r, t, key_tc, key_tau, gid, closer))
                     accept<N, COUNT>(a, r, pass, closer, t, key_tc, key_tau, alpha, gid, cnt.draws);
             }
-            G = r.t_far >= r.t_min ? r.t_far : -INFINITY;
+            // the group clip moves only when some lane's clip did
+            if (__any_sync(gmask, r.t_far != far0)) {
+                G = r.t_far >= r.t_min ? r.t_far : -INFINITY;
 #pragma unroll
-            for (int o = 1; o < L; o <<= 1) G = fmaxf(G, __shfl_xor_sync(gmask, G, o));
+                for (int o = 1; o < L; o <<= 1) G = fmaxf(G, __shfl_xor_sync(gmask, G, o));
+            }
         }
         const bool inner = hit && !leaf && te <= G;
         const uint32_t im = (__ballot_sync(gmask, inner) >> base) & kLaneBits;
