@@ -36,14 +36,17 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     # -ffp-contract=off: no fused multiply-add, so the float32 camera-ray
     # definition rounds after every operation on every architecture.
+    # a temporary of this process, renamed atomically: processes that build
+    # at the same time do not write the same file
+    tmp = "%s.%d.tmp" % (_LIB_PATH, os.getpid())
     base = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
-            "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", _LIB_PATH + ".tmp", "-lm"]
+            "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
                        capture_output=True, text=True)
     except subprocess.CalledProcessError:
         subprocess.run(base, check=True, capture_output=True, text=True)
-    os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
 

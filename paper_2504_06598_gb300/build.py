@@ -6,6 +6,7 @@ library under ``_build/`` next to this file. Nothing is installed."""
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import shutil
 import subprocess
@@ -41,10 +42,24 @@ def _deps():
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Build libgsrt.so if any source is newer than it. Returns its path."""
+    """Build libgsrt.so if any source is newer than it. Returns its path.
+
+    Processes that build at the same time (ranks of one job) serialise on a
+    lock file; the ones that wait find the library up to date."""
     os.makedirs(BUILD, exist_ok=True)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
         return LIB
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
+                return LIB
+            return _build_locked(verbose, extra_flags)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose, extra_flags) -> str:
     nvcc = nvcc_path()
 
     def compile_one(src):
