@@ -219,7 +219,8 @@ gs_status gs_bvh_sync_status(gs_bvh *bvh, void *stream);
  *   codes_out  host uint64[M]: sorted Morton codes, or NULL
  *   order_out  host uint32[M]: Gaussian id of each leaf position, or NULL
  * Node record (64 bytes): float box[2][6] as {lo.x,lo.y,lo.z,hi.x,hi.y,
- * hi.z} of the left then right child, uint32 child[2], uint32 reserved[2];
+ * hi.z} of the left then right child, uint32 child[2], uint32 leaf_range[2]
+ * (the first and last leaf position the node covers);
  * a child reference with bit 31 set is leaf (ref & 0x7fffffff), else an
  * internal node index; node 0 is the root. */
 gs_status gs_bvh_export(const gs_bvh *bvh, void *nodes_out, void *prims_out,

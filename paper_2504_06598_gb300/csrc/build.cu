@@ -368,8 +368,8 @@ __global__ void k_karras(int64_t n, const unsigned long long *__restrict__ codes
     Node &nd = nodes[i];
     nd.child[0] = left;
     nd.child[1] = right;
-    nd.reserved[0] = 0;
-    nd.reserved[1] = 0;
+    nd.leaf_range[0] = (uint32_t)lo;
+    nd.leaf_range[1] = (uint32_t)hi;
     if (left & kLeafBit) parent_leaf[gamma] = (uint32_t)i; else parent_int[gamma] = (uint32_t)i;
     if (right & kLeafBit) parent_leaf[gamma + 1] = (uint32_t)i; else parent_int[gamma + 1] = (uint32_t)i;
 }
@@ -441,7 +441,7 @@ __global__ void k_single(const uint32_t *__restrict__ order, const float *__rest
         for (int k = 0; k < 6; ++k) nd.box[s][k] = aabb[6 * (int64_t)g + k];
         nd.child[s] = kLeafBit;
     }
-    nd.reserved[0] = nd.reserved[1] = 0;
+    nd.leaf_range[0] = nd.leaf_range[1] = 0;
     nodes[0] = nd;
 }
 
@@ -549,10 +549,14 @@ __global__ void k_collapse(int64_t n_int, const Node *__restrict__ nodes,
     }
 }
 
-// The W-wide hierarchies (W = 2^LEVELS): one wide node per binary internal
-// node at depth 0 mod LEVELS, whose children are its descendants LEVELS
-// levels down, or the leaves met before. expand_wide lists them, left to
-// right, with their boxes.
+// The W-wide hierarchies (W = 2^LEVELS). The wide nodes sit at binary
+// internal nodes of depth 0 mod LEVELS; a wide node covering at most W
+// leaves has those leaves as its children (and no wide node below it),
+// any other has its descendants LEVELS levels down, or the leaves met
+// before. So a binary node is a wide root when it is the root, or when its
+// depth is 0 mod LEVELS and its ancestor LEVELS levels up covers more than
+// W leaves. expand_wide lists the LEVELS-level children, left to right,
+// with their boxes.
 template <int LEVELS>
 __device__ __forceinline__ int expand_wide(const Node *__restrict__ nodes, uint32_t i,
                                            uint32_t ref[1 << LEVELS], float box[1 << LEVELS][6]) {
@@ -600,19 +604,36 @@ __global__ void k_node_depth(int64_t n_int, const uint32_t *__restrict__ parent_
     depth[i] = d;
 }
 
+__device__ __forceinline__ uint32_t leaves_under(const Node &nd) {
+    return nd.leaf_range[1] - nd.leaf_range[0] + 1u;
+}
+
 // Children of the wide node at each binary internal node (0 where none);
 // the same count seeds the offsets.
 template <int LEVELS>
 __global__ void k_count_wide(int64_t n_int, const Node *__restrict__ nodes,
-                             const uint32_t *__restrict__ depth, uint32_t *__restrict__ cnt,
+                             const uint32_t *__restrict__ depth,
+                             const uint32_t *__restrict__ parent_int, uint32_t *__restrict__ cnt,
                              uint32_t *__restrict__ off) {
+    constexpr uint32_t W = 1u << LEVELS;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_int) return;
     uint32_t c = 0;
-    if (depth[i] % (uint32_t)LEVELS == 0u) {
-        uint32_t ref[1 << LEVELS];
-        float box[1 << LEVELS][6];
-        c = (uint32_t)expand_wide<LEVELS>(nodes, (uint32_t)i, ref, box);
+    bool root = i == 0;
+    if (!root && depth[i] % (uint32_t)LEVELS == 0u) {
+        uint32_t p = (uint32_t)i;
+        for (int k = 0; k < LEVELS; ++k) p = parent_int[p];
+        root = leaves_under(nodes[p]) > W;
+    }
+    if (root) {
+        const uint32_t n_leaves = leaves_under(nodes[i]);
+        if (n_leaves <= W) {
+            c = n_leaves;
+        } else {
+            uint32_t ref[1 << LEVELS];
+            float box[1 << LEVELS][6];
+            c = (uint32_t)expand_wide<LEVELS>(nodes, (uint32_t)i, ref, box);
+        }
     }
     cnt[i] = c;
     off[i] = c;
@@ -622,13 +643,28 @@ __global__ void k_count_wide(int64_t n_int, const Node *__restrict__ nodes,
 template <int LEVELS>
 __global__ void k_collapse_wide(int64_t n_int, const Node *__restrict__ nodes,
                                 const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ off,
+                                const uint32_t *__restrict__ order, const float *__restrict__ aabb,
                                 ChildRec *__restrict__ rec) {
+    constexpr uint32_t W = 1u << LEVELS;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_int || cnt[i] == 0u) return;
+    ChildRec *dst = rec + off[i];
+    const Node ndi = nodes[i];
+    if (leaves_under(ndi) <= W) {
+        // every leaf of the node, with the box its parent node holds for it
+        for (uint32_t k = ndi.leaf_range[0]; k <= ndi.leaf_range[1]; ++k) {
+            ChildRec c;
+            const float *b = aabb + 6 * (int64_t)order[k];
+            for (int q = 0; q < 3; ++q) { c.lo[q] = b[q]; c.hi[q] = b[3 + q]; }
+            c.child = kLeafBit | k;
+            c.reserved = 0;
+            *dst++ = c;
+        }
+        return;
+    }
     uint32_t ref[1 << LEVELS];
     float box[1 << LEVELS][6];
     const int n = expand_wide<LEVELS>(nodes, (uint32_t)i, ref, box);
-    ChildRec *dst = rec + off[i];
     for (int j = 0; j < n; ++j) {
         ChildRec c;
         for (int q = 0; q < 3; ++q) { c.lo[q] = box[j][q]; c.hi[q] = box[j][3 + q]; }
@@ -723,15 +759,21 @@ gs_status build_into(gs_bvh *b, const gs_gaussians *g, cudaStream_t s) {
         const int64_t n_int = b->n_nodes;
         k_node_depth<<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->parent, b->node_depth);
         const GroupTree *t = b->group;
-        k_count_wide<3><<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->nodes, b->node_depth, t[0].cnt, t[0].off);
+        k_count_wide<3><<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->nodes, b->node_depth, b->parent,
+                                                            t[0].cnt, t[0].off);
         scan_exclusive(t[0].off, n_int, b->scan_tmp, s);
-        k_collapse_wide<3><<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->nodes, t[0].cnt, t[0].off, t[0].rec);
-        k_count_wide<4><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, b->node_depth, t[1].cnt, t[1].off);
+        k_collapse_wide<3><<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->nodes, t[0].cnt, t[0].off,
+                                                               order, b->aabb, t[0].rec);
+        k_count_wide<4><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, b->node_depth, b->parent,
+                                                            t[1].cnt, t[1].off);
         scan_exclusive(t[1].off, n_int, b->scan_tmp, s);
-        k_collapse_wide<4><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, t[1].cnt, t[1].off, t[1].rec);
-        k_count_wide<5><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, b->node_depth, t[2].cnt, t[2].off);
+        k_collapse_wide<4><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, t[1].cnt, t[1].off,
+                                                               order, b->aabb, t[1].rec);
+        k_count_wide<5><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, b->node_depth, b->parent,
+                                                            t[2].cnt, t[2].off);
         scan_exclusive(t[2].off, n_int, b->scan_tmp, s);
-        k_collapse_wide<5><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, t[2].cnt, t[2].off, t[2].rec);
+        k_collapse_wide<5><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, t[2].cnt, t[2].off,
+                                                               order, b->aabb, t[2].rec);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "build launch");
     return GS_OK;

@@ -30,7 +30,7 @@ static_assert(sizeof(PrimRec) == 64, "PrimRec must be 64 bytes");
 struct __align__(16) Node {
     float box[2][6];  // {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z} left, right
     uint32_t child[2];
-    uint32_t reserved[2];
+    uint32_t leaf_range[2];  // first and last sorted leaf the node covers
 };
 static_assert(sizeof(Node) == 64, "Node must be 64 bytes");
 

@@ -51,6 +51,13 @@ def _check_tree(ex, M):
     internal_refs = np.sort(idx[~leaf])
     assert np.array_equal(internal_refs, np.arange(1, n))
     assert np.array_equal(np.sort(idx[leaf]), np.arange(M))
+    # each node covers a contiguous leaf range: the left child's, then the right's
+    rng = nodes[:, 14:16].astype(np.int64)
+    assert rng[0, 0] == 0 and rng[0, 1] == M - 1
+    lo_of = lambda s: np.where(leaf[:, s], idx[:, s], rng[idx[:, s] * (~leaf[:, s]), 0])  # noqa: E731
+    hi_of = lambda s: np.where(leaf[:, s], idx[:, s], rng[idx[:, s] * (~leaf[:, s]), 1])  # noqa: E731
+    assert np.array_equal(lo_of(0), rng[:, 0]) and np.array_equal(hi_of(1), rng[:, 1])
+    assert np.array_equal(hi_of(0) + 1, lo_of(1))
     # parent slot box contains the child's own box (the union of its slots)
     for i in range(n):
         for s in range(2):
