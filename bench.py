@@ -4,7 +4,7 @@
 Workload: 1,000,000 Gaussians in 64 clusters on a unit-sphere shell (SH
 degree 3, float32), one 1920x1080 pinhole view from distance 3, 60 degree
 vertical FOV. One step = hierarchy rebuild over all Gaussians + one
-stochastic trace of the view with N=1 and spp=64 (the north-star metric);
+stochastic trace of the view with N=1 and spp=64 (the headline metric);
 N=4 at spp=16 (the same 64 samples per pixel) is timed the same way and
 reported beside it.
 
