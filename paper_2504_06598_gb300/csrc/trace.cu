@@ -45,10 +45,13 @@ __host__ __device__ constexpr bool is_group_fmt(int f) { return f >= kFmtGroup +
 // Persistent kernel: each warp repeatedly takes the next tile (one atomic
 // per tile, so the tail of the launch stays balanced), then runs all passes
 // of its pixels. The grouped form is latency-bound and is built for eight
-// resident blocks per SM (five with eight slots per lane), the per-lane
-// packet form for five (up to four slots).
+// resident blocks per SM with one or two slots per lane (64 registers),
+// seven with four (72: fewer spills of the four slots), five with eight;
+// the per-lane packet form for five (up to four slots).
+constexpr int group_min_blocks(int n) { return n >= 8 ? 5 : (n >= 4 ? 7 : kGroupMinBlocks); }
+
 template <int N, bool COUNT, int FMT>
-__global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? (N >= 8 ? 5 : kGroupMinBlocks)
+__global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? group_min_blocks(N)
                                                                : (N >= 8 ? 1 : 5))
     k_trace(const TraceArgs a) {
     const int lane = threadIdx.x & 31;
