@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? group_min_blocks
             if (!live) r.t_far = -INFINITY;  // lanes off the image never hit
             if (a.n_nodes > 0) {
                 if constexpr (grouped)
-                    traverse_group<N, COUNT, LG>(a, r, pass, grp_ref, grp_t, err, cnt);
+                    traverse_group<N, COUNT, LG, true>(a, r, pass, grp_ref, grp_t, err, cnt);
                 else if constexpr (FMT == GS_NODES_BINARY)
                     traverse_packet<N, COUNT>(a, r, pass, stack, stack_t, err, cnt);
                 else

@@ -798,7 +798,9 @@ constexpr int kGroupMinBlocks = 8; // resident blocks per SM to build for
 // inner children go to the group's stack in shared memory. Every node and
 // leaf a lane's own ray needs is visited, and each lane keeps its own slots
 // and clip, so per-lane results are those of an independent traversal.
-template <int N, bool COUNT, int LG>
+// POP2 selects the two-stage pop of the group stack (below); both pop the
+// same entries.
+template <int N, bool COUNT, int LG, bool POP2 = false>
 __device__ __forceinline__ void traverse_group(const TraceArgs &a, Ray<N> &r, int pass,
                                                uint32_t *s_ref, float *s_t, uint32_t &err,
                                                Counts &cnt) {
@@ -912,15 +914,48 @@ __device__ __forceinline__ void traverse_group(const TraceArgs &a, Ray<N> &r, in
             node_t = next_t;
             continue;
         }
+        // pop the topmost entry within the group clip, dropping the ones
+        // above it
         bool found = false;
-        while (sp > 0) {
-            --sp;
-            const float tt = s_t[sp];
-            if (tt <= G) {
-                node = s_ref[sp];
-                node_t = tt;
-                found = true;
-                break;
+        if constexpr (POP2) {
+            // the top entry alone first (it usually holds); past it, lane k
+            // checks the k-th entry below, one step per L culled entries
+            if (sp > 0) {
+                const float tt = s_t[sp - 1];
+                if (tt <= G) {
+                    --sp;
+                    node = s_ref[sp];
+                    node_t = tt;
+                    found = true;
+                } else {
+                    --sp;
+                }
+            }
+            if (!found)
+                while (sp > 0) {
+                    const int k = sp - 1 - sub;
+                    const float tt = k >= 0 ? s_t[k] : INFINITY;
+                    const uint32_t okm = (__ballot_sync(gmask, tt <= G) >> base) & kLaneBits;
+                    if (okm) {
+                        const int j = __ffs(okm) - 1;  // the lowest lane holds the topmost
+                        sp = sp - 1 - j;
+                        node = s_ref[sp];
+                        node_t = s_t[sp];
+                        found = true;
+                        break;
+                    }
+                    sp = sp > L ? sp - L : 0;
+                }
+        } else {
+            while (sp > 0) {
+                --sp;
+                const float tt = s_t[sp];
+                if (tt <= G) {
+                    node = s_ref[sp];
+                    node_t = tt;
+                    found = true;
+                    break;
+                }
             }
         }
         if (!found) break;
