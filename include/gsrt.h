@@ -299,17 +299,22 @@ gs_status gs_trace_backward(const gs_bvh *bvh, const gs_gaussians *g, const gs_p
  *   nodes_out  device, max(M-1, 1) * 64 bytes, 16-byte aligned: node
  *              records in the gs_bvh_export layout, node 0 the root
  *   prims_out  device, M * 64 bytes, 16-byte aligned: Gaussian records
- *   status_out optional device uint32: the caller clears it; the build ORs
- *              error bits into it (non-zero means a non-finite parameter)
+ *   status_out device uint32, required (NULL returns GS_ERR_INVALID_ARG):
+ *              the caller clears it; the build ORs error bits into it
+ *              (non-zero means a non-finite parameter)
  *   stream     where the kernels are enqueued
  * Scratch memory lives in one statically allocated device array of this
  * library (about 4 MB on every GPU that loads the library, held until the
- * process exits). The first call on each device looks up that array's
- * device address (cudaGetSymbolAddress), so make it before any stream
- * capture. Every call shares the array: calls whose work overlaps on the
- * GPU (different streams, or different host threads) race and corrupt each
- * other; serialise them, for example on one stream. No cudaMalloc, cudaFree
- * or other allocating call is made. */
+ * process exits). The first call on each device loads the library's module
+ * there (CUDA loads modules lazily) and looks up that array's device address
+ * (cudaGetSymbolAddress); loading a module may itself allocate and
+ * synchronise, so make one warm-up call per device before the region that
+ * must not allocate, and before any stream capture. The address is cached
+ * per device and is invalid after cudaDeviceReset. Every call shares the
+ * array: calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race and corrupt each other; serialise them, for
+ * example on one stream. No cudaMalloc, cudaFree or other allocating call is
+ * made. */
 gs_status gs_build_bvh_noalloc(const gs_gaussians *g, void *nodes_out, void *prims_out,
                                uint32_t *status_out, void *stream);
 

@@ -3,10 +3,11 @@
 // Same kernels and results as gs_build_bvh, for callers that must not call
 // cudaMalloc: the caller passes the output buffers, and the build scratch
 // (sort keys and ids, parents, arrival counters, boxes, histograms, scan
-// block sums, status)
-// lives in one file-scope __device__ array sized for at most
+// block sums) lives in one file-scope __device__ array sized for at most
 // kNoAllocMaxGaussians Gaussians. Every GPU that loads this library holds
-// that array (about 4 MB) until the process exits.
+// that array (about 4 MB) until the process exits. The caller's status word
+// receives the build's error bits, so it is required: with no word of its
+// own a caller would never learn of a non-finite parameter.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -34,8 +35,7 @@ constexpr size_t kHist = kBounds + align_up(64);
 constexpr size_t kHistEntries = 256 * ((kNoAllocMaxGaussians + 2047) / 2048);
 constexpr size_t kScanTmp = kHist + align_up(4 * kHistEntries);
 constexpr size_t kScanTmpEntries = kHistEntries / 1024 + 2;
-constexpr size_t kStatus = kScanTmp + align_up(4 * kScanTmpEntries);
-constexpr size_t kScratchBytes = kStatus + align_up(16);
+constexpr size_t kScratchBytes = kScanTmp + align_up(4 * kScanTmpEntries);
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -44,7 +44,11 @@ std::mutex g_setup_mutex;
 void *g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once
-// per device (the symbol's host-side name is not a device address).
+// per device (the symbol's host-side name is not a device address). With
+// CUDA's lazy module loading this first lookup is also what loads the
+// library's module on that device, which can allocate and synchronise; the
+// cached address is that of the device's primary context and is stale after
+// a cudaDeviceReset.
 gs_status scratch_address(unsigned char **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -90,7 +94,10 @@ extern "C" gs_status gs_build_bvh_noalloc(const gs_gaussians *g, void *nodes_out
                            prims_out};
     for (const void *p : ptrs)
         if (!is_device_ptr(p)) return fail(GS_ERR_INVALID_ARG, "an argument is not a device pointer");
-    if (status_out && !is_device_ptr(status_out))
+    if (!status_out)
+        return fail(GS_ERR_INVALID_ARG,
+                    "status_out is NULL: the build reports non-finite parameters through it");
+    if (!is_device_ptr(status_out))
         return fail(GS_ERR_INVALID_ARG, "status_out is not a device pointer");
 
     unsigned char *s = nullptr;
@@ -113,11 +120,6 @@ extern "C" gs_status gs_build_bvh_noalloc(const gs_gaussians *g, void *nodes_out
     b.hist_len = (int64_t)kHistEntries;
     b.scan_tmp = reinterpret_cast<uint32_t *>(s + kScanTmp);
     b.node_format = GS_NODES_BINARY;
-    b.status = status_out ? status_out : reinterpret_cast<uint32_t *>(s + kStatus);
-    if (!status_out) {
-        // the shared status word keeps the last call's contents: clear it
-        cudaError_t e = cudaMemsetAsync(b.status, 0, 4, (cudaStream_t)stream);
-        if (e != cudaSuccess) return cuda_fail(e, "clear status");
-    }
+    b.status = status_out;
     return build_into(&b, g, (cudaStream_t)stream);
 }
