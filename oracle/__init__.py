@@ -99,6 +99,8 @@ def _load():
             lib.orc_bounce_dir.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, P]
             lib.orc_hash_xi.restype = C.c_double
             lib.orc_hash_xi.argtypes = [P, C.c_uint32]
+            lib.orc_hash_constants.restype = None
+            lib.orc_hash_constants.argtypes = [P]
             lib.orc_render_scene.restype = C.c_int
             lib.orc_render_scene.argtypes = [P, P, C.c_int32, P, P, C.c_int64, P, P, P, P, C.c_int]
             lib.orc_render_rays.restype = C.c_int
@@ -411,3 +413,12 @@ def hash_xi(p, sample):
     """The trigonometric hash draw (Eq. 8-9) of hit position p for a sample."""
     q = _c(p, np.float64)
     return float(_load().orc_hash_xi(_ptr(q), int(sample)))
+
+
+def hash_constants():
+    """The coefficients of Eq. 8-9 the oracle's hash uses:
+    {"a1", "b1", "a2": [2], "b2": [2]}."""
+    out = np.zeros(6, np.float64)
+    _load().orc_hash_constants(_ptr(out))
+    return {"a1": float(out[0]), "b1": float(out[1]), "a2": [float(out[2]), float(out[3])],
+            "b2": [float(out[4]), float(out[5])]}

@@ -126,13 +126,29 @@ double orc_xi(uint64_t seed, uint32_t ray_id, uint32_t gid, uint32_t sample, uin
 
 /* Trigonometric hash of a hit position (Sec. 4.2, Eq. 8-9):
  *   r1(q) = fract(b1 sin(a1 q)), r2(q) = fract(b2 sin(a2^T q)),
- *   xi(p) = r2(p_xy + r1(p_z)), a1 = 91.3458, b1 = 47453.5453,
- *   a2 = (12.9898, 78.233), b2 = 43758.5453 (both entries equal, so both
- *   components of r2 are equal; the first is used).
+ *   xi(p) = r2(p_xy + r1(p_z)),
+ * with the coefficients the paper states after Eq. 9 (below). Both entries
+ * of b2 are equal, so both components of r2 are equal; the first is used.
  * The paper makes the draws change between frames by jittering the camera
  * rays; here the rays are fixed, so sample s hashes p + delta_s, with
  * delta_s = 1e-3 * (frac(s c1), frac(s c2), frac(s c3)) - 5e-4 from the
  * additive recurrence with c = (0.8191725134, 0.6710436067, 0.5497004779). */
+static const double kHashA1 = 91.3458;
+static const double kHashB1 = 47453.5453;
+static const double kHashA2[2] = {12.9898, 78.233};
+static const double kHashB2[2] = {43758.5453, 43758.5453};
+
+/* The coefficients orc_hash_xi uses: a1, b1, a2[0], a2[1], b2[0], b2[1]. */
+void orc_hash_constants(double out[6])
+{
+    out[0] = kHashA1;
+    out[1] = kHashB1;
+    out[2] = kHashA2[0];
+    out[3] = kHashA2[1];
+    out[4] = kHashB2[0];
+    out[5] = kHashB2[1];
+}
+
 static double fract_d(double x) { return x - floor(x); }
 
 double orc_hash_xi(const double p[3], uint32_t sample)
@@ -140,9 +156,9 @@ double orc_hash_xi(const double p[3], uint32_t sample)
     const double c[3] = {0.8191725134, 0.6710436067, 0.5497004779};
     double q[3];
     for (int i = 0; i < 3; ++i) q[i] = p[i] + 1e-3 * fract_d((double)sample * c[i]) - 5e-4;
-    double r1 = fract_d(47453.5453 * sin(91.3458 * q[2]));
+    double r1 = fract_d(kHashB1 * sin(kHashA1 * q[2]));
     double x = q[0] + r1, y = q[1] + r1;
-    return fract_d(43758.5453 * sin(12.9898 * x + 78.233 * y));
+    return fract_d(kHashB2[0] * sin(kHashA2[0] * x + kHashA2[1] * y));
 }
 
 /* Camera forward axis of a pinhole, float32 as in orc_camera_ray. */

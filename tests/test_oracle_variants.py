@@ -1,7 +1,13 @@
 """Pins of the oracle's variants: the projected-centre depth of Sec. 4.1
 (depth order of two Gaussians where the 1D-mean order and the centre order
 differ, composited by hand), and the trigonometric hash draw of Eq. 8-9
-(range, uniformity, per-sample variation, approximate unbiasedness)."""
+(its coefficients against the values the paper prints; range, uniformity,
+per-sample variation, approximate unbiasedness). The composition
+r2(p_xy + r1(p_z)) itself is pinned only statistically: the paper prints no
+hash values to compare with."""
+import json
+import os
+
 import numpy as np
 from scipy.spatial.transform import Rotation
 
@@ -34,6 +40,14 @@ def test_centre_depth_changes_the_order(oracle_lib):
     centre_mode = oracle_lib.render_pinhole(cloud, cam, scenes.TraceSettings(depth_mode=1))
     assert np.allclose(mean_mode["blend"][0], aA * cA + (1 - aA) * aB * cB, atol=1e-12)
     assert np.allclose(centre_mode["blend"][0], aB * cB + (1 - aB) * aA * cA, atol=1e-12)
+
+
+def test_hash_constants_match_the_paper(oracle_lib):
+    path = os.path.join(os.path.dirname(__file__), "golden", "trig_hash_constants.json")
+    gold = json.load(open(path))
+    got = oracle_lib.hash_constants()
+    assert got["a1"] == gold["a1"] and got["b1"] == gold["b1"]
+    assert got["a2"] == gold["a2"] and got["b2"] == gold["b2"]
 
 
 def test_hash_draws(oracle_lib):
