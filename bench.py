@@ -54,6 +54,10 @@ def parse():
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--n-hits", type=int, default=1, help="N of the profiling case")
     ap.add_argument("--case-spp", type=int, default=1, help="spp of the profiling case")
+    ap.add_argument("--record-counters", default=None, metavar="CSV",
+                    help="store the per-launch metrics of an `ncu --csv --print-units base "
+                         "--metrics ...` log of a trace case under --key (no GPU needed)")
+    ap.add_argument("--key", default=None, help="trace launch of --record-counters, e.g. n1_spp64")
     ap.add_argument("--workload", choices=["shell-1m", "precision-3m", "wavefront-16v",
                                            "backward-1m"],
                     default="shell-1m",
@@ -380,18 +384,114 @@ def trace_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(n_hits):
-    """DRAM bytes per launch of the trace kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "trace_traffic.json")
+COUNTER_FILE = ("profiles", "trace_counters.json")
+# per-launch ncu metrics of the trace kernel recorded by --record-counters
+COUNTER_METRICS = ("smsp__inst_executed.sum",
+                   "smsp__issue_active.avg.pct_of_peak_sustained_active",
+                   "smsp__thread_inst_executed_per_inst_executed.ratio",
+                   "lts__t_bytes.sum", "dram__bytes_read.sum", "dram__bytes_write.sum",
+                   "gpu__time_duration.sum")
+_UNIT_SCALE = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "tbyte": 1e12,
+               "nsecond": 1.0, "usecond": 1e3, "msecond": 1e6, "second": 1e9,
+               "inst": 1.0, "kinst": 1e3, "minst": 1e6, "ginst": 1e9,
+               "%": 1.0, "": 1.0}
+
+
+def recorded_counters(key):
+    """Per-launch ncu counters of the trace launch `key` (e.g. "n1_spp64")
+    from the committed record, if they were taken on the current kernel
+    source; else None."""
+    path = os.path.join(ROOT, *COUNTER_FILE)
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
     if rec.get("source_hash") != trace_source_hash():
         return None
-    entry = rec.get("n%d" % n_hits)
-    return None if entry is None else entry.get("dram_bytes_per_launch")
+    return rec.get("launches", {}).get(key)
+
+
+def recorded_traffic(key):
+    """DRAM bytes (read + write) per launch of trace launch `key`, or None."""
+    c = recorded_counters(key)
+    return None if c is None else c.get("dram_bytes")
+
+
+def parse_ncu_csv(path):
+    """Metric values per captured launch from an `ncu --csv --metrics` log:
+    {launch id: {metric: value in base units (bytes, ns, instructions)}}."""
+    import csv
+    rows = {}
+    with open(path, newline="") as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        name, unit, val = r.get("Metric Name"), (r.get("Metric Unit") or "").lower(), r.get("Metric Value")
+        if not name or val is None:
+            continue
+        try:
+            v = float(val.replace(",", ""))
+        except ValueError:
+            continue
+        rows.setdefault(r["ID"], {})[name] = v * _UNIT_SCALE.get(unit, 1.0)
+    return rows
+
+
+def record_counters(csv_path, key, layout=None):
+    """Average the launches of an ncu metrics log into the committed record
+    under `key`, stamped with the current trace source hash (a record for an
+    older source is dropped)."""
+    launches = parse_ncu_csv(csv_path)
+    if not launches:
+        raise SystemExit("no metric rows in %s" % csv_path)
+    mean = lambda m: float(np.mean([v[m] for v in launches.values() if m in v]))  # noqa: E731
+    entry = {"inst_executed": mean("smsp__inst_executed.sum"),
+             "issue_active_pct": mean("smsp__issue_active.avg.pct_of_peak_sustained_active"),
+             "thread_inst_per_inst": mean("smsp__thread_inst_executed_per_inst_executed.ratio"),
+             "lts_bytes": mean("lts__t_bytes.sum"),
+             "dram_read_bytes": mean("dram__bytes_read.sum"),
+             "dram_write_bytes": mean("dram__bytes_write.sum"),
+             "duration_ns_under_ncu": mean("gpu__time_duration.sum"),
+             "launches": len(launches)}
+    entry["dram_bytes"] = entry["dram_read_bytes"] + entry["dram_write_bytes"]
+    if layout:
+        entry["layout"] = layout
+    path = os.path.join(ROOT, *COUNTER_FILE)
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        rec = {}
+    h = trace_source_hash()
+    if rec.get("source_hash") != h:
+        rec = {"source_hash": h, "launches": {}}
+    rec["launches"][key] = entry
+    with open(path, "w") as f:
+        json.dump(rec, f, indent=1, sort_keys=True)
+        f.write("\n")
+    return entry
+
+
+def measure_copy_peaks(gs, dev):
+    """Copy bandwidth of this GPU measured with the library's own probe
+    kernel: L2-resident (16 MiB + 16 MiB, repeated in one launch) and
+    DRAM-resident (1 GiB + 1 GiB), best of five, read + write bytes."""
+    import torch
+    out = {}
+    for name, nbytes, reps in (("l2", 16 << 20, 400), ("dram", 1 << 30, 2)):
+        src = torch.ones(nbytes // 4, dtype=torch.float32, device=dev)
+        dst = torch.empty_like(src)
+        gs.probe_copy(src, dst, repeats=1)
+        best = 0.0
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gs.probe_copy(src, dst, repeats=reps)
+            e1.record()
+            e1.synchronize()
+            best = max(best, 2.0 * nbytes * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+        out[name + "_copy_gbs"] = best
+        del src, dst
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args, rank, world):
@@ -435,6 +535,9 @@ def run_reference(args, rank, world):
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.record_counters:
+        print(json.dumps(record_counters(args.record_counters, args.key)))
+        return
     if args.case:
         run_case(args)
         return
@@ -473,6 +576,10 @@ def main():
     bvh.sync_status()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     rgb = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32, device=dev)
+    props = torch.cuda.get_device_properties(dev)
+    n_sms = props.multi_processor_count
+    peaks = measure_copy_peaks(gs, dev)
+    hbm_peak, hbm_kind = measured_peak()
 
     def step(n_hits, spp, events=None):
         if events:
@@ -484,31 +591,31 @@ def main():
         if events:
             events[2].record(stream)
 
-    # instrumented launches (untimed): node / primitive / shading counts of
-    # the timed launches (grouped traversal: child records), and of the same
-    # rays' own traversals of the binary hierarchy (per-lane packets at spp
-    # 2, with the same per-sample hits), which define the algorithmic bytes
-    def counted(n_hits, spp):
+    # instrumented launches (untimed): node / primitive / shading counts per
+    # lane walk of the timed launch, and of one sample's own traversal of
+    # the binary hierarchy (per-lane packets at spp 2, one sample per lane,
+    # the same per-sample hits), which defines the algorithmic bytes
+    def counted(n_hits, spp, samples_per_lane=0):
         cnt = torch.zeros(7, dtype=torch.int64, device=dev)
-        gs.trace_stochastic(bvh, g, cam, seed=0, spp=spp, n_hits=n_hits, out=rgb, counters=cnt)
+        gs.trace_stochastic(bvh, g, cam, seed=0, spp=spp, n_hits=n_hits, out=rgb, counters=cnt,
+                            samples_per_lane=samples_per_lane)
         bvh.sync_status()
         c = cnt.cpu().numpy().astype(np.float64)
         return {"nodes": c[0], "prims": c[1], "philox": c[2], "rays": c[3],
                 "shaded": c[4], "node_fetch": c[5], "prim_fetch": c[6], "spp": spp}
 
-    visits = {1: counted(1, SPP_N1), 4: counted(4, SPP_N4)}
-    binary = {1: counted(1, 2), 4: counted(4, 2)}
+    binary = {1: counted(1, 2, 1), 4: counted(4, 2, 1)}
 
-    def timed(n_hits, spp):
+    def timed(n_hits, spp, steps):
         for _ in range(args.warmup):
             step(n_hits, spp)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
         with ClockSampler(local) as clk:
-            for k in range(args.steps):
+            for k in range(steps):
                 flush.fill_(float(k))
                 step(n_hits, spp, evs[k])
             torch.cuda.synchronize()
@@ -523,9 +630,81 @@ def main():
             [res["step_ms"], res["trace_ms"]], device=dev)
         return res
 
+    info = bvh.info()
+    sh_bytes = 16 * 3 * 4
+
+    def roof(n_hits, spp, trace_ms, clocks):
+        """Roofline of the trace launch: the binding level (instruction issue:
+        one warp instruction per SM sub-partition per cycle at the SM clock
+        sampled during the run) from the recorded per-launch counters, with
+        the L2 and DRAM levels against this run's copy peaks beside it."""
+        key = "n%d_spp%d" % (n_hits, spp)
+        bv = binary[n_hits if n_hits in binary else 1]
+        # algorithmic bytes per sample: 64 B per binary node its own
+        # traversal enters, 64 B per Gaussian tested, one SH record per
+        # shaded sample, plus each pixel's 12-byte output
+        per_ray = (info["node_bytes"] * bv["nodes"] + info["prim_bytes"] * bv["prims"]
+                   + sh_bytes * bv["shaded"]) / (bv["rays"] * bv["spp"])
+        alg = per_ray * npix * spp + 12 * npix
+        sec = trace_ms * 1e-3
+        mhz = clocks.get("sm_mhz") or 2070.0
+        issue_peak = n_sms * 4 * mhz * 1e6 / 1e9
+        out = {"bound": "alu", "limiter": "instruction issue (warp instructions per SM "
+                                          "sub-partition per cycle)",
+               "achieved": None, "peak": issue_peak, "unit": "Gwarp-inst/s", "frac": None,
+               "traffic": None, "kernel": "k_trace (%s)" % key,
+               "peak_basis": "%d SMs x 4 schedulers x 1 warp-inst/cycle x %.0f MHz sampled"
+                             % (n_sms, mhz),
+               "alg_bytes_per_ray": per_ray, "alg_bytes_per_launch": alg,
+               "alg_gbs_useful": alg / sec / 1e9,
+               "binary_nodes_per_ray": bv["nodes"] / (bv["rays"] * bv["spp"]),
+               "gaussians_tested_per_ray": bv["prims"] / (bv["rays"] * bv["spp"])}
+        c = recorded_counters(key)
+        if c is None:
+            out["counters"] = "not captured on this kernel source"
+            return out
+        out["achieved"] = c["inst_executed"] / sec / 1e9
+        out["frac"] = out["achieved"] / issue_peak
+        out["traffic"] = c["dram_bytes"]
+        out["issue_active_pct_ncu"] = c["issue_active_pct"]
+        out["simt_lanes_per_inst"] = c["thread_inst_per_inst"]
+        out["warp_inst_per_sample"] = c["inst_executed"] / (npix * spp)
+        out["l2"] = {"achieved_gbs": c["lts_bytes"] / sec / 1e9, "peak_gbs": peaks["l2_copy_gbs"],
+                     "frac": c["lts_bytes"] / sec / 1e9 / peaks["l2_copy_gbs"],
+                     "peak_kind": "measured (library copy probe, 32 MiB L2-resident)",
+                     "bytes_per_launch": c["lts_bytes"]}
+        out["dram"] = {"achieved_gbs": c["dram_bytes"] / sec / 1e9, "peak_gbs": hbm_peak,
+                       "frac": c["dram_bytes"] / sec / 1e9 / hbm_peak, "peak_kind": hbm_kind,
+                       "bytes_per_launch": c["dram_bytes"]}
+        return out
+
+    def record(n_hits, spp, steps):
+        """Timing, layout, visit counts and roofline of one trace launch."""
+        v = counted(n_hits, spp)
+        r = timed(n_hits, spp, steps)
+        lay = gs.trace_layout(bvh, spp=spp, n_hits=n_hits)
+        share = lay["samples_per_lane"] * (lay["lanes_per_pixel"] if lay["grouped"] else 1)
+        walks = npix * -(-spp // share)
+        sec = r["trace_ms"] * 1e-3
+        return {"spp": spp, "n_hits": n_hits, "ms_per_step": r["step_ms"],
+                "build_ms": r["build_ms"], "trace_ms": r["trace_ms"],
+                "mrays_per_s": npix * spp * world / (r["step_ms"] * 1e-3) / 1e6,
+                "msamples_per_s": npix * spp * n_hits * world / (r["step_ms"] * 1e-3) / 1e6,
+                "trace_mrays_per_s": npix * spp / sec / 1e6,
+                "layout": lay,
+                # walks of the hierarchy: one per group of lanes sharing a
+                # ray when grouped, one per lane otherwise
+                "walks_per_s": walks / sec, "samples_per_walk": npix * spp / walks,
+                "visits_per_walk": {"node_records": v["nodes"] / walks,
+                                    "prims": v["prims"] / walks,
+                                    "philox": v["philox"] / walks},
+                "roofline": roof(n_hits, spp, r["trace_ms"], r["clocks"]),
+                "clocks": r["clocks"]}
+
     bvh.sync_status()
-    r1 = timed(1, SPP_N1)
-    r4 = timed(4, SPP_N4)
+    r1 = record(1, SPP_N1, args.steps)
+    r4 = record(4, SPP_N4, args.steps)
+    ladder = {"n1_spp1": record(1, 1, args.steps), "n1_spp16": record(1, 16, args.steps)}
     bvh.sync_status()
 
     # end to end through the public API: pinned host inputs, result read back
@@ -552,75 +731,32 @@ def main():
     e2e_mean = parallel.max_over_ranks([float(np.mean(e2e_ms))], device=dev)[0]
 
     rays_step = npix * SPP_N1 * world
-    value = rays_step / (r1["step_ms"] * 1e-3) / 1e6
+    value = rays_step / (r1["ms_per_step"] * 1e-3) / 1e6
     # this library's kernels per step: the rebuild (preprocess, key, 8 radix
     # passes of histogram + 3-kernel scan + scatter, Karras, leaves, node
     # depths, and count + 3-kernel scan + collapse for each of the three
     # wide copies) and one trace
     launches_per_step = 2 + 8 * 5 + 2 + 1 + 3 * 5 + 1
 
-    # roofline of the trace kernel: algorithmic bytes per launch / duration
-    peak, peak_kind = measured_peak()
-    info = bvh.info()
-    sh_bytes = 16 * 3 * 4
-
-    def roof(v, trace_ms, n_hits):
-        # algorithmic bytes per ray, from the binary hierarchy (the method's
-        # own traversal, whatever layout the kernel reads): 64 B per node
-        # entered, 64 B per Gaussian tested, one SH record per shaded sample,
-        # plus each pixel's 12-byte output
-        bv = binary[n_hits]
-        per_ray = (info["node_bytes"] * bv["nodes"] + info["prim_bytes"] * bv["prims"]
-                   + sh_bytes * bv["shaded"]) / (bv["rays"] * bv["spp"])
-        alg = per_ray * npix * v["spp"] + 12 * npix
-        # bytes the groups of the timed launch request: one 32-byte child
-        # record per fetch (spp >= 8 runs the grouped traversal)
-        rec = 32 if (info["node_format"] == 0 and v["spp"] >= 8) else info["node_bytes"]
-        warp = (rec * v["node_fetch"] + info["prim_bytes"] * v["prim_fetch"]
-                + sh_bytes * v["shaded"] + 12 * npix)
-        ach = alg / (trace_ms * 1e-3) / 1e9
-        traffic = recorded_traffic(n_hits)
-        out = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-               "frac": ach / peak, "traffic": traffic,
-               "alg_bytes_per_launch": alg, "warp_request_bytes_per_launch": warp,
-               "warp_request_gbs": warp / (trace_ms * 1e-3) / 1e9,
-               "peak_kind": peak_kind, "kernel": "k_trace<%d>" % n_hits,
-               "alg_bytes_per_ray": per_ray,
-               # rays per second HBM could feed if every algorithmic byte came from DRAM
-               "hbm_ceiling_mrays_per_s": peak * 1e9 / per_ray / 1e6,
-               "binary_nodes_per_ray": bv["nodes"] / (bv["rays"] * bv["spp"]),
-               "gaussians_tested_per_ray": bv["prims"] / (bv["rays"] * bv["spp"])}
-        if traffic is not None:
-            # what DRAM actually moved (ncu counters) over this run's duration
-            out["dram_gbs"] = traffic / (trace_ms * 1e-3) / 1e9
-            out["dram_frac"] = out["dram_gbs"] / peak
-        return out
-
     line = {
         "metric": "Mrays/s at 1M Gaussians 1080p (N=1,4); RMSE vs exact blend at equal time",
         "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": r1["step_ms"], "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": r1["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_dict(args, world), "clocks": r1["clocks"],
         "e2e": {"value": rays_step / (e2e_mean * 1e-3) / 1e6, "unit": "Mrays/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": e2e_mean},
         "gpu_launches": launches_per_step * args.steps,
-        "roofline": roof(visits[1], r1["trace_ms"], 1),
+        "roofline": r1["roofline"],
+        "copy_peaks_gbs": peaks,
         "build_ms": r1["build_ms"], "trace_ms": r1["trace_ms"],
-        "trace_mrays_per_s": npix * SPP_N1 / (r1["trace_ms"] * 1e-3) / 1e6,
-        "visits_per_ray": {"node_records": visits[1]["nodes"] / visits[1]["rays"] / SPP_N1,
-                           "prims": visits[1]["prims"] / visits[1]["rays"] / SPP_N1,
-                           "philox": visits[1]["philox"] / visits[1]["rays"] / SPP_N1,
-                           "fetched_node_records_per_ray": visits[1]["node_fetch"] / visits[1]["rays"] / SPP_N1},
-        "n4": {"spp": SPP_N4, "samples_per_pixel": SPP_N4 * 4, "ms_per_step": r4["step_ms"],
-               "trace_ms": r4["trace_ms"],
-               "mrays_per_s": npix * SPP_N4 * world / (r4["step_ms"] * 1e-3) / 1e6,
-               "msamples_per_s": npix * SPP_N4 * 4 * world / (r4["step_ms"] * 1e-3) / 1e6,
-               "roofline": roof(visits[4], r4["trace_ms"], 4),
-               "visits_per_ray": {"node_records": visits[4]["nodes"] / visits[4]["rays"] / SPP_N4,
-                                  "prims": visits[4]["prims"] / visits[4]["rays"] / SPP_N4},
-               "clocks": r4["clocks"]},
+        "trace_mrays_per_s": r1["trace_mrays_per_s"],
+        "layout": r1["layout"], "walks_per_s": r1["walks_per_s"],
+        "samples_per_walk": r1["samples_per_walk"], "visits_per_walk": r1["visits_per_walk"],
+        "n4": r4,
+        "n1_spp1": ladder["n1_spp1"],
+        "n1_spp16": ladder["n1_spp16"],
         "msamples_per_s_n1": value,
     }
 

@@ -120,6 +120,18 @@ typedef struct gs_pinhole {
  *                 1e-3 * frac(s * (0.8191725134, 0.6710436067,
  *                 0.5497004779)) - 5e-4 (gs_trace_stochastic only; float32,
  *                 not reproducible bit for bit)
+ *   samples_per_lane
+ *                 how many consecutive samples one lane of a traversal
+ *                 carries (gs_trace_stochastic only): 1, 2, 4 or 8 with
+ *                 n_hits * samples_per_lane <= 8, or 0 to let the library
+ *                 choose. The pixel then takes ceil(spp / S) passes, each
+ *                 with n_hits * S slots (samples pass*n_hits*S + k),
+ *                 so the S samples share one walk and one Philox call
+ *                 serves four of their draws. Per-sample hits do not depend
+ *                 on S; rgb_out may differ in the last bits (summation
+ *                 order). The counters then count each lane's walk (the
+ *                 union of its S samples' traversals); pass 1 for counts of
+ *                 one sample's own traversal.
  *   counters      optional device uint64[7], incremented by the launch:
  *                 {nodes entered by each ray's own traversal, Gaussians
  *                 tested (Alg. 1 runs), Philox calls, rays (pixels),
@@ -140,6 +152,7 @@ typedef struct gs_trace_params {
     int32_t stack_depth;
     uint32_t stream_tag;
     int32_t rng_mode;
+    int32_t samples_per_lane;
     unsigned long long *counters;
 } gs_trace_params;
 
@@ -247,8 +260,8 @@ gs_status gs_bvh_export_wide(const gs_bvh *bvh, void *out, int64_t capacity, int
  *              sample's hit (ray parameter, d is unit length) or +inf;
  *              NULL to skip
  * The 32 lanes of a warp split into pixels x samples: the L lanes of a pixel
- * (L the largest power of two not above spp, at most 32) trace passes
- * j*L + lane of the same ray. With L >= 8 and a GS_NODES_BINARY handle a
+ * (L the largest power of two not above ceil(spp / S), at most 32, S =
+ * samples_per_lane) trace passes j*L + lane of the same ray. With L >= 8 and a GS_NODES_BINARY handle a
  * group of L lanes traverses the L-wide copy together (each lane tests one
  * child box, evaluates one hit Gaussian's depth and alpha, and draws for its
  * own samples); otherwise each lane traverses the nodes of the handle's
@@ -259,6 +272,25 @@ gs_status gs_bvh_export_wide(const gs_bvh *bvh, void *out, int64_t capacity, int
 gs_status gs_trace_stochastic(const gs_bvh *bvh, const gs_gaussians *g, const gs_pinhole *cam,
                               const gs_trace_params *p, float *rgb_out, int32_t *hit_id_out,
                               float *hit_t_out, void *stream);
+
+/* How gs_trace_stochastic(bvh, ..., p, ...) maps samples to lanes (host
+ * call, nothing is enqueued). layout_out (host int32[4]) receives
+ * {samples per lane S, lanes per pixel L, passes ceil(spp / S) of
+ * n_hits * S slots each, 1 if a group of L lanes walks the L-wide copy
+ * together else 0}: one walk
+ * of the hierarchy serves L * S samples of one ray when grouped, S samples
+ * otherwise. Returns GS_ERR_INVALID_ARG for NULL pointers or options
+ * gs_trace_stochastic would reject. */
+gs_status gs_trace_layout(const gs_bvh *bvh, const gs_trace_params *p, int32_t *layout_out);
+
+/* Measurement support (the paper has no counterpart): copy `bytes` from
+ * src to dst `repeats` times in one kernel with 16-byte loads and stores
+ * that bypass L1, enqueued on `stream`. src and dst are device pointers,
+ * 16-byte aligned, bytes a positive multiple of 16, repeats in 1..2^20.
+ * With src + dst well inside L2 the copy measures L2 bandwidth (the
+ * denominator of the trace kernel's L2 roofline), beyond L2 it measures
+ * DRAM bandwidth. The caller times it (for example with CUDA events). */
+gs_status gs_probe_copy(const void *src, void *dst, int64_t bytes, int32_t repeats, void *stream);
 
 /* Unbiased stochastic gradient of an image loss (the differentiable
  * rendering extension named at the end of the paper, Sec. 6). For each

@@ -54,7 +54,8 @@ class _TraceParams(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("spp", C.c_int32), ("n_hits", C.c_int32),
                 ("t_min", C.c_float), ("t_max", C.c_float), ("bg", C.c_float * 3),
                 ("depth_mode", C.c_int32), ("stack_depth", C.c_int32),
-                ("stream_tag", C.c_uint32), ("rng_mode", C.c_int32), ("counters", C.c_void_p)]
+                ("stream_tag", C.c_uint32), ("rng_mode", C.c_int32),
+                ("samples_per_lane", C.c_int32), ("counters", C.c_void_p)]
 
 
 class _BvhInfo(C.Structure):
@@ -100,6 +101,8 @@ _SIGNATURES = {
                                          C.c_void_p, C.c_void_p, C.c_void_p]),
     "gs_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gs_graph_free": (C.c_int, [C.c_void_p]),
+    "gs_trace_layout": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_probe_copy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
     "gs_status_string": (C.c_char_p, [C.c_int]),
     "gs_last_error": (C.c_char_p, []),
 }
@@ -195,7 +198,7 @@ class Camera:
 
 def _params(seed=0, spp=1, n_hits=1, t_min=0.0, t_max=float("inf"), bg=(0.0, 0.0, 0.0),
             stack_depth=0, stream_tag=0, counters=None, depth_mode=0,
-            rng_mode=0) -> _TraceParams:
+            rng_mode=0, samples_per_lane=0) -> _TraceParams:
     p = _TraceParams()
     p.seed = int(seed)
     p.spp = int(spp)
@@ -207,6 +210,7 @@ def _params(seed=0, spp=1, n_hits=1, t_min=0.0, t_max=float("inf"), bg=(0.0, 0.0
     p.stack_depth = int(stack_depth)
     p.stream_tag = int(stream_tag)
     p.rng_mode = int(rng_mode)
+    p.samples_per_lane = int(samples_per_lane)
     p.counters = None if counters is None else counters.data_ptr()
     return p
 
@@ -294,7 +298,7 @@ def build_bvh(g: Gaussians, stream=None, node_format="binary") -> Bvh:
 def trace_stochastic(bvh: Bvh, g: Gaussians, cam, seed=0, spp=1, n_hits=1, t_min=0.0,
                      t_max=float("inf"), bg=(0.0, 0.0, 0.0), stack_depth=0, stream_tag=0,
                      want_hits=False, counters=None, out=None, stream=None, depth_mode=0,
-                     rng_mode=0):
+                     rng_mode=0, samples_per_lane=0):
     """``gs_trace_stochastic``: render one pinhole view.
 
     Returns ``rgb`` [H, W, 3] float32 (and ``hit_id``, ``hit_t`` of shape
@@ -310,7 +314,7 @@ def trace_stochastic(bvh: Bvh, g: Gaussians, cam, seed=0, spp=1, n_hits=1, t_min
     gs = g.struct()
     cs = cam.struct()
     ps = _params(seed, spp, n_hits, t_min, t_max, bg, stack_depth, stream_tag, counters,
-                 depth_mode, rng_mode)
+                 depth_mode, rng_mode, samples_per_lane)
     _check(lib().gs_trace_stochastic(
         bvh.handle, C.byref(gs), C.byref(cs), C.byref(ps), C.c_void_p(rgb.data_ptr()),
         None if hit_id is None else C.c_void_p(hit_id.data_ptr()),
@@ -318,6 +322,26 @@ def trace_stochastic(bvh: Bvh, g: Gaussians, cam, seed=0, spp=1, n_hits=1, t_min
     if want_hits:
         return rgb, hit_id, hit_t
     return rgb
+
+
+def trace_layout(bvh: Bvh, spp=1, n_hits=1, samples_per_lane=0) -> dict:
+    """``gs_trace_layout``: how a trace with these options maps samples to
+    lanes (samples per lane, lanes per pixel, passes of n_hits * S slots,
+    grouped)."""
+    ps = _params(0, spp, n_hits, samples_per_lane=samples_per_lane)
+    out = (C.c_int32 * 4)()
+    _check(lib().gs_trace_layout(bvh.handle, C.byref(ps), out))
+    return {"samples_per_lane": out[0], "lanes_per_pixel": out[1], "passes": out[2],
+            "grouped": bool(out[3])}
+
+
+def probe_copy(src, dst, repeats=1, stream=None):
+    """``gs_probe_copy``: enqueue a copy of ``src`` into ``dst`` (device
+    tensors of equal byte size) repeated ``repeats`` times in one kernel."""
+    nbytes = src.numel() * src.element_size()
+    assert dst.numel() * dst.element_size() == nbytes
+    _check(lib().gs_probe_copy(C.c_void_p(src.data_ptr()), C.c_void_p(dst.data_ptr()),
+                               nbytes, int(repeats), _stream_handle(stream)))
 
 
 def trace_backward(bvh: Bvh, g: Gaussians, cam, d_rgb, seed=0, spp=1, n_hits=1, t_min=0.0,

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgsrt.so")
-SOURCES = ["api.cu", "build.cu", "trace.cu", "backward.cu", "wavefront.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "build.cu", "trace.cu", "backward.cu", "wavefront.cu", "noalloc.cu",
+           "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -334,6 +334,14 @@ static gs_status check_trace_args(const gs_bvh *b, const gs_gaussians *g, const 
         return fail(GS_ERR_INVALID_ARG, "depth_mode=%d unsupported", p->depth_mode);
     if (p->rng_mode != 0 && p->rng_mode != 1)
         return fail(GS_ERR_INVALID_ARG, "rng_mode=%d unsupported", p->rng_mode);
+    {
+        const int S = p->samples_per_lane;
+        if (S != 0 && S != 1 && S != 2 && S != 4 && S != 8)
+            return fail(GS_ERR_INVALID_ARG, "samples_per_lane=%d must be 0, 1, 2, 4 or 8", S);
+        if (S * p->n_hits > 8)
+            return fail(GS_ERR_INVALID_ARG, "n_hits * samples_per_lane = %d exceeds 8",
+                        S * p->n_hits);
+    }
     if (isnan(p->t_min) || isnan(p->t_max) || !(p->t_min < p->t_max))
         return fail(GS_ERR_INVALID_ARG, "need t_min < t_max");
     return GS_OK;
@@ -355,6 +363,24 @@ gs_status gs_trace_stochastic(const gs_bvh *b, const gs_gaussians *g, const gs_p
     if (p->counters && !is_device_ptr(p->counters))
         return fail(GS_ERR_INVALID_ARG, "counters is not a device pointer");
     return launch_trace(b, g, cam, p, rgb_out, hit_id_out, hit_t_out, (cudaStream_t)stream);
+}
+
+gs_status gs_trace_layout(const gs_bvh *b, const gs_trace_params *p, int32_t *layout_out) {
+    if (!b || !p || !layout_out) return fail(GS_ERR_INVALID_ARG, "bvh, params or layout_out is NULL");
+    if (p->spp < 1 || p->spp > (1 << 20)) return fail(GS_ERR_INVALID_ARG, "spp=%d out of range", p->spp);
+    if (p->n_hits != 1 && p->n_hits != 2 && p->n_hits != 4 && p->n_hits != 8)
+        return fail(GS_ERR_INVALID_ARG, "n_hits=%d must be 1, 2, 4 or 8", p->n_hits);
+    const int S0 = p->samples_per_lane;
+    if ((S0 != 0 && S0 != 1 && S0 != 2 && S0 != 4 && S0 != 8) || S0 * p->n_hits > 8)
+        return fail(GS_ERR_INVALID_ARG, "samples_per_lane=%d invalid for n_hits=%d", S0, p->n_hits);
+    int S = 1, spp_eff = 1, lg = 0;
+    bool grouped = false;
+    trace_layout(b, p, &S, &spp_eff, &lg, &grouped);
+    layout_out[0] = S;
+    layout_out[1] = 1 << lg;
+    layout_out[2] = spp_eff;
+    layout_out[3] = grouped ? 1 : 0;
+    return GS_OK;
 }
 
 gs_status gs_trace_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,

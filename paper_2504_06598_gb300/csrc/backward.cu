@@ -549,6 +549,7 @@ gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinho
     a.key1 = (uint32_t)(p->seed >> 32);
     a.stream_tag = p->stream_tag;
     a.spp = p->spp;
+    a.n_samples = p->spp * p->n_hits;
     a.t_min = p->t_min;
     a.t_max = p->t_max;
     a.stack_depth = p->stack_depth == 0 ? kMaxStack : p->stack_depth;

@@ -179,6 +179,10 @@ gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_p
                               int32_t *samples, cudaStream_t s);
 
 // Trace (trace.cu)
+// How a trace with these options maps samples to lanes: S samples per lane,
+// spp_eff passes, 2^lpp_log2 lanes per pixel, grouped (cooperative) traversal.
+void trace_layout(const gs_bvh *b, const gs_trace_params *p, int *S, int *spp_eff,
+                  int *lpp_log2, bool *grouped);
 gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
                        const gs_trace_params *p, float *rgb, int32_t *hit_id, float *hit_t,
                        cudaStream_t s);

@@ -101,8 +101,13 @@ __global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? group_min_blocks
         for (int j = 0; j < n_rounds; ++j) {
             const int pass = (j << lg) + sub;
             const bool live = valid && pass < a.spp;
+            const int s0 = pass * N;
+            // an unused slot (sample index beyond the pixel's count) sits
+            // at -inf: no candidate is closer, and it never sets the clip
 #pragma unroll
-            for (int k = 0; k < N; ++k) r.slot[k] = Slot{INFINITY, INFINITY, 0.0f, 0xffffffffu};
+            for (int k = 0; k < N; ++k)
+                r.slot[k] = s0 + k < a.n_samples ? Slot{INFINITY, INFINITY, 0.0f, 0xffffffffu}
+                                                 : Slot{-INFINITY, -INFINITY, 0.0f, 0xffffffffu};
             update_clip(r, a.t_max);
             if (!live) r.t_far = -INFINITY;  // lanes off the image never hit
             if (a.n_nodes > 0) {
@@ -119,6 +124,7 @@ __global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? group_min_blocks
                 sh_basis(a.sh_degree, r.d, Y);
 #pragma unroll
                 for (int k = 0; k < N; ++k) {
+                    if (s0 + k >= a.n_samples) continue;
                     float c[3];
                     if (r.slot[k].gid != 0xffffffffu) {
                         sh_colour(a, r.slot[k].gid, Y, c);
@@ -130,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? group_min_blocks
                     acc[1] += c[1];
                     acc[2] += c[2];
                     if (a.hit_id) {
-                        const int64_t o = ((int64_t)pass * N + k) * npix + pix;
+                        const int64_t o = ((int64_t)s0 + k) * npix + pix;
                         a.hit_id[o] = r.slot[k].gid == 0xffffffffu ? -1 : (int32_t)r.slot[k].gid;
                         a.hit_t[o] = r.slot[k].t;
                     }
@@ -145,7 +151,7 @@ __global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? group_min_blocks
             acc[2] += __shfl_xor_sync(kAll, acc[2], o);
         }
         if (valid && sub == 0) {
-            const float inv_n = 1.0f / (float)((int64_t)a.spp * N);
+            const float inv_n = 1.0f / (float)a.n_samples;
             a.rgb[3 * pix + 0] = acc[0] * inv_n;
             a.rgb[3 * pix + 1] = acc[1] * inv_n;
             a.rgb[3 * pix + 2] = acc[2] * inv_n;
@@ -203,15 +209,41 @@ gs_status launch_n(const TraceArgs &a, int format, bool count, cudaStream_t s) {
     }
 }
 
+// Samples one lane carries when the caller leaves the choice to the
+// library (samples_per_lane = 0).
+int auto_samples_per_lane(int spp, int n_hits, int node_format) {
+    (void)spp;
+    (void)n_hits;
+    (void)node_format;
+    return 1;
+}
+
 }  // namespace
+
+void trace_layout(const gs_bvh *b, const gs_trace_params *p, int *S_out, int *spp_eff_out,
+                  int *lpp_log2_out, bool *grouped_out) {
+    // A lane carries S consecutive samples: the launch runs ceil(spp / S)
+    // passes of n_hits * S slots; sample s = pass * n_hits * S + k either way.
+    int S = p->samples_per_lane > 0 ? p->samples_per_lane
+                                    : auto_samples_per_lane(p->spp, p->n_hits, b->node_format);
+    while (S > 1 && S > p->spp) S >>= 1;
+    *S_out = S;
+    *spp_eff_out = (p->spp + S - 1) / S;
+    *lpp_log2_out = lanes_per_pixel_log2(*spp_eff_out);
+    *grouped_out = b->node_format == GS_NODES_BINARY && b->node_depth && *lpp_log2_out >= 3;
+}
 
 gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
                        const gs_trace_params *p, float *rgb, int32_t *hit_id, float *hit_t,
                        cudaStream_t s) {
+    int S = 1, spp_eff = 1, lpp_log2 = 0;
+    bool grouped = false;
+    trace_layout(b, p, &S, &spp_eff, &lpp_log2, &grouped);
+    const int n_eff = p->n_hits * S;
     TraceArgs a;
     a.nodes = b->nodes;
     a.wide = b->wide;
-    a.lpp_log2 = lanes_per_pixel_log2(p->spp);
+    a.lpp_log2 = lpp_log2;
     if (b->node_depth && a.lpp_log2 >= 3) {
         a.grec = b->group[a.lpp_log2 - 3].rec;
         a.gcnt = b->group[a.lpp_log2 - 3].cnt;
@@ -237,7 +269,8 @@ gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole 
     a.key0 = (uint32_t)(p->seed & 0xffffffffu);
     a.key1 = (uint32_t)(p->seed >> 32);
     a.stream_tag = p->stream_tag;
-    a.spp = p->spp;
+    a.spp = spp_eff;
+    a.n_samples = p->spp * p->n_hits;
     a.t_min = p->t_min;
     a.t_max = p->t_max;
     a.stack_depth = p->stack_depth == 0 ? kMaxStack : p->stack_depth;
@@ -263,7 +296,7 @@ gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole 
     }
     const bool count = p->counters != nullptr;
     gs_status st;
-    switch (p->n_hits) {
+    switch (n_eff) {
         case 1: st = launch_n<1>(a, b->node_format, count, s); break;
         case 2: st = launch_n<2>(a, b->node_format, count, s); break;
         case 4: st = launch_n<4>(a, b->node_format, count, s); break;

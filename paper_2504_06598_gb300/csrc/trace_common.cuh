@@ -31,7 +31,8 @@ struct TraceArgs {
     float eye[3], look_at[3], up[3];
     float tan_half;
     uint32_t key0, key1, stream_tag;
-    int spp;
+    int spp;        // passes per pixel of the launch (each with N slots)
+    int n_samples;  // samples per pixel; slots at s = pass * N + k >= n_samples are unused
     float t_min, t_max;
     float bg[3];
     int stack_depth;

@@ -594,6 +594,7 @@ gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_p
     a.key1 = (uint32_t)(p->seed >> 32);
     a.stream_tag = p->stream_tag;
     a.spp = p->spp;
+    a.n_samples = p->spp;
     a.t_min = p->t_min;
     a.t_max = p->t_max;
     const int stack = (opt && opt->stack_entries == 48) ? 48 : 96;

@@ -110,6 +110,45 @@ def test_grouped_and_packet_traversals_agree(gs):
     assert np.array_equal(ta, tb) and np.array_equal(ta, tc)
 
 
+@pytest.mark.parametrize("spp,n_hits", [(64, 1), (16, 1), (5, 1), (33, 1), (8, 2), (3, 2), (16, 4),
+                                        (10, 1)])
+def test_samples_per_lane_mappings_agree(gs, spp, n_hits):
+    """A lane carrying S consecutive samples (S slots per pass, ceil(spp/S)
+    passes, unused slots past the pixel's last sample) returns the hits and
+    depths of one sample per lane; the pixel means differ only in summation
+    order."""
+    cloud = scenes.shell_cloud(7, M=20000)
+    cam = scenes.default_camera(52, 37)
+    r1, a1, t1 = _run(gs, cloud, cam, spp=spp, n_hits=n_hits, seed=3, samples_per_lane=1)
+    for S in (2, 4, 8):
+        if S * n_hits > 8:
+            continue
+        rS, aS, tS = _run(gs, cloud, cam, spp=spp, n_hits=n_hits, seed=3, samples_per_lane=S)
+        assert np.array_equal(a1, aS), S
+        assert np.array_equal(t1, tS), S
+        assert np.allclose(r1, rS, rtol=1e-6, atol=1e-7), S
+    # the library's own choice
+    r0, a0, t0 = _run(gs, cloud, cam, spp=spp, n_hits=n_hits, seed=3)
+    assert np.array_equal(a1, a0) and np.array_equal(t1, t0)
+    assert np.allclose(r1, r0, rtol=1e-6, atol=1e-7)
+
+
+def test_trace_layout_reports_the_mapping(gs):
+    g = gs.Gaussians.from_cloud(scenes.shell_cloud(7, M=5000))
+    bvh = gs.build_bvh(g)
+    lay = gs.trace_layout(bvh, spp=64, n_hits=1, samples_per_lane=4)
+    assert lay == {"samples_per_lane": 4, "lanes_per_pixel": 16, "passes": 16,
+                   "grouped": True}
+    lay = gs.trace_layout(bvh, spp=3, n_hits=1, samples_per_lane=1)
+    assert lay == {"samples_per_lane": 1, "lanes_per_pixel": 2, "passes": 3,
+                   "grouped": False}
+    # S is capped at spp; invalid combinations are rejected
+    assert gs.trace_layout(bvh, spp=2, n_hits=1, samples_per_lane=8)["samples_per_lane"] == 2
+    with pytest.raises(gs.GsError):
+        gs.trace_layout(bvh, spp=8, n_hits=4, samples_per_lane=4)
+    bvh.free()
+
+
 def test_deterministic(gs):
     cloud = scenes.shell_cloud(3, M=5000)
     cam = scenes.default_camera(40, 30)
