@@ -103,6 +103,8 @@ def _load():
             lib.orc_hash_constants.argtypes = [P]
             lib.orc_render_scene.restype = C.c_int
             lib.orc_render_scene.argtypes = [P, P, C.c_int32, P, P, C.c_int64, P, P, P, P, C.c_int]
+            lib.orc_scene_sample_rays.restype = C.c_int
+            lib.orc_scene_sample_rays.argtypes = [P, P, P, C.c_int32, C.c_int32, C.c_uint32, P]
             lib.orc_render_rays.restype = C.c_int
             lib.orc_render_rays.argtypes = [P, P, C.c_int64, P, P, P, P, P, P, P, P, P, C.c_int]
             _lib = lib
@@ -400,6 +402,24 @@ def render_scene(cloud, cams, extras, settings, items, want_diag=True, n_threads
     lib.orc_render_scene(h.ref, arr, len(cams), C.byref(ex), C.byref(ps), n, _ptr(v), _ptr(px),
                          _ptr(est), _ptr(diag), int(n_threads))
     return {"est": est, "diag": diag}
+
+
+def scene_sample_rays(cam, extras, settings, x, y, sample):
+    """The float32 rays of one sample of the scene renderer: camera ray,
+    ground hit, shadow rays to each light and the bounce direction."""
+    out = np.zeros(46, np.float32)
+    ps = _params(settings)
+    cs = _pinhole(cam)
+    ex = _extras(extras)
+    ground = _load().orc_scene_sample_rays(C.byref(cs), C.byref(ex), C.byref(ps), int(x), int(y),
+                                           int(sample), _ptr(out))
+    lights = []
+    for l in range(len(extras.lights)):
+        v = out[14 + 4 * l: 18 + 4 * l]
+        lights.append(None if v[3] < 0 else (v[:3].copy(), float(v[3])))
+    return {"o": out[0:3].copy(), "d": out[3:6].copy(), "ray_id": int(out[6:7].view(np.uint32)[0]),
+            "ground": bool(ground), "tq": float(out[7]), "p": out[8:11].copy(),
+            "bounce_d": out[11:14].copy(), "lights": lights}
 
 
 def bounce_dir(seed, ray_id, sample):

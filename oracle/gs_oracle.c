@@ -1030,6 +1030,84 @@ void orc_bounce_dir(uint64_t seed, uint32_t ray_id, uint32_t s, float d[3])
     for (int i = 0; i < 3; ++i) d[i] = b[i] / n;
 }
 
+/* Ground point of a float32 camera ray (o, d): tq = (ground_y - o.y) / d.y,
+ * p = o + tq d with p.y = ground_y, each operation rounded once in float32.
+ * Returns 1 when the ray meets the quad inside its range, else 0 (tq is
+ * then +inf). */
+static int ground_point(const orc_extras *ex, const float o[3], const float d[3], double t_min,
+                        float *tq_out, float gp[3])
+{
+    int ground = 0;
+    float tq = INFINITY;
+    gp[0] = gp[1] = gp[2] = 0.0f;
+    if (ex && ex->has_ground && d[1] != 0.0f) {
+        tq = (ex->ground_y - o[1]) / d[1];
+        float ax = tq * d[0], az = tq * d[2];
+        gp[0] = o[0] + ax;
+        gp[1] = ex->ground_y;
+        gp[2] = o[2] + az;
+        ground = (double)tq > t_min && fabsf(gp[0]) <= ex->ground_half_extent &&
+                 fabsf(gp[2]) <= ex->ground_half_extent;
+        if (!ground) tq = INFINITY;
+    }
+    *tq_out = tq;
+    return ground;
+}
+
+/* Shadow ray from ground point gp to light l in float32: unit direction om,
+ * distance dist and its square. Returns 0 when the light is not above the
+ * ground (no contribution). */
+static int light_ray(const orc_extras *ex, int l, const float gp[3], float om[3], float *dist_out,
+                     float *dist2_out)
+{
+    float w[3];
+    for (int i = 0; i < 3; ++i) w[i] = ex->lights[l].position[i] - gp[i];
+    float dist2 = w[0] * w[0];
+    dist2 = dist2 + w[1] * w[1];
+    dist2 = dist2 + w[2] * w[2];
+    float dist = sqrtf(dist2);
+    for (int i = 0; i < 3; ++i) om[i] = w[i] / dist;
+    *dist_out = dist;
+    *dist2_out = dist2;
+    return om[1] > 0.0f && dist2 > 0.0f;
+}
+
+/* Exported for the tests' mismatch classifier: the float32 rays of sample s
+ * of pixel (x, y) of a camera in the scene renderer. out[46]:
+ *   [0..2] camera origin, [3..5] camera direction, [6] ray id (its bits),
+ *   [7] ground tq (+inf when the quad is missed), [8..10] ground point,
+ *   [11..13] bounce direction, and per light l < 8: [14 + 4l .. 16 + 4l]
+ *   the shadow ray's direction, [17 + 4l] its length, or -1 when light l
+ *   does not contribute. Returns 1 when the camera ray meets the ground. */
+int orc_scene_sample_rays(const orc_pinhole *cam, const orc_extras *ex, const orc_params *p,
+                          int32_t x, int32_t y, uint32_t s, float *out)
+{
+    double od[3], dd[3];
+    uint32_t rid;
+    orc_camera_ray(cam, x, y, od, dd, &rid);
+    float o[3] = {(float)od[0], (float)od[1], (float)od[2]};
+    float d[3] = {(float)dd[0], (float)dd[1], (float)dd[2]};
+    for (int i = 0; i < 3; ++i) {
+        out[i] = o[i];
+        out[3 + i] = d[i];
+    }
+    memcpy(&out[6], &rid, sizeof(rid));
+    float tq, gp[3];
+    int ground = ground_point(ex, o, d, p->t_min, &tq, gp);
+    out[7] = tq;
+    for (int i = 0; i < 3; ++i) out[8 + i] = gp[i];
+    float db[3];
+    orc_bounce_dir(p->seed, rid, s, db);
+    for (int i = 0; i < 3; ++i) out[11 + i] = db[i];
+    for (int l = 0; l < 8; ++l) {
+        float om[3] = {0.0f, 0.0f, 0.0f}, dist = -1.0f, dist2 = 0.0f;
+        int ok = ground && ex && l < ex->n_lights && light_ray(ex, l, gp, om, &dist, &dist2);
+        for (int i = 0; i < 3; ++i) out[14 + 4 * l + i] = om[i];
+        out[14 + 4 * l + 3] = ok ? dist : -1.0f;
+    }
+    return ground;
+}
+
 /* Exported: render items (view[i], pix[i]) of the given cameras.
  * est [n][3]; diag [n][spp][3] = {camera hit (id, -2 ground, -1 none),
  * bounce hit (id or -1), visible-light bits} (nullable). */
@@ -1058,18 +1136,8 @@ int orc_render_scene(const orc_scene *sc, const orc_pinhole *cams, int32_t n_vie
         float o[3] = {(float)od[0], (float)od[1], (float)od[2]};
         float d[3] = {(float)dd[0], (float)dd[1], (float)dd[2]};
         /* ground point in float32 */
-        int ground = 0;
-        float tq = INFINITY, gp[3] = {0.0f, 0.0f, 0.0f};
-        if (ex && ex->has_ground && d[1] != 0.0f) {
-            tq = (ex->ground_y - o[1]) / d[1];
-            float ax = tq * d[0], az = tq * d[2];
-            gp[0] = o[0] + ax;
-            gp[1] = ex->ground_y;
-            gp[2] = o[2] + az;
-            ground = (double)tq > p->t_min && fabsf(gp[0]) <= ex->ground_half_extent &&
-                     fabsf(gp[2]) <= ex->ground_half_extent;
-            if (!ground) tq = INFINITY;
-        }
+        float tq, gp[3];
+        int ground = ground_point(ex, o, d, p->t_min, &tq, gp);
         double acc[3] = {0.0, 0.0, 0.0};
         for (int32_t s = 0; s < S; ++s) {
             double tg;
@@ -1087,14 +1155,8 @@ int orc_render_scene(const orc_scene *sc, const orc_pinhole *cams, int32_t n_vie
                 c[0] = c[1] = c[2] = 0.0;
                 dcam = -2;
                 for (int l = 0; l < ex->n_lights; ++l) {
-                    float w[3], om[3];
-                    for (int i = 0; i < 3; ++i) w[i] = ex->lights[l].position[i] - gp[i];
-                    float dist2 = w[0] * w[0];
-                    dist2 = dist2 + w[1] * w[1];
-                    dist2 = dist2 + w[2] * w[2];
-                    float dist = sqrtf(dist2);
-                    for (int i = 0; i < 3; ++i) om[i] = w[i] / dist;
-                    if (!(om[1] > 0.0f && dist2 > 0.0f)) continue;
+                    float om[3], dist, dist2;
+                    if (!light_ray(ex, l, gp, om, &dist, &dist2)) continue;
                     int64_t blocker = accepted_on_ray(sc, act, gp, om, ex->shadow_eps, dist, p->seed,
                                                       rid, (uint32_t)s, 1u + (uint32_t)l, 1, NULL);
                     if (blocker >= 0) continue;

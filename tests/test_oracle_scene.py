@@ -80,3 +80,55 @@ def test_empty_scene_ground_radiance(oracle_lib):
     want = np.array(ex.ground_albedo) / np.pi * np.array(light[1]) * cosv / (w @ w) \
         + np.array(ex.ground_albedo) * 1.0
     assert np.allclose(r["est"][0], want, rtol=1e-6)
+
+
+def _winner(oracle_lib, cloud, o, d, rid, s, seed, tag, t_min, t_max, any_hit=False):
+    c = oracle_lib.ray_candidates(cloud, o, d, t_min=t_min, t_max=t_max)
+    acc = [(t, int(g)) for t, g, a in zip(c["t"], c["gid"], c["alpha"])
+           if oracle_lib.xi(seed, rid, int(g), s, tag) < a]
+    if not acc:
+        return -1, np.inf
+    t, g = min(acc)
+    return g, t
+
+
+def test_sample_rays_reproduce_the_renderers_outcomes(oracle_lib):
+    """The exported per-sample rays (used to classify GPU mismatches) are
+    the renderer's own: re-deciding each sample from them with the pinned
+    candidate list and draws gives the renderer's camera hit, bounce hit
+    and visible-light bits; a planted wrong outcome is classified 'other'."""
+    from tests import _parity
+    cloud = scenes.shell_cloud(7, M=3000)
+    cams = scenes.wavefront_views(2, seed=2, res_range=((9, 7), (14, 10)))
+    ex = scenes.ground_and_lights(4, seed=1)
+    st = scenes.TraceSettings(seed=5, spp=3)
+    items = [(v, p) for v, c in enumerate(cams) for p in range(c.width * c.height)]
+    diag = oracle_lib.render_scene(cloud, cams, ex, st, items)["diag"]
+    n_ground = 0
+    for i, (v, p) in enumerate(items):
+        for s in range(st.spp):
+            cam = cams[v]
+            r = oracle_lib.scene_sample_rays(cam, ex, st, p % cam.width, p // cam.width, s)
+            g, t = _winner(oracle_lib, cloud, r["o"], r["d"], r["ray_id"], s, st.seed, 0,
+                           st.t_min, np.inf)
+            ground = r["ground"] and not (g >= 0 and t < r["tq"])
+            cam_out = -2 if ground else g
+            bounce, bits = -1, 0
+            if ground:
+                n_ground += 1
+                bounce, _ = _winner(oracle_lib, cloud, r["p"], r["bounce_d"], r["ray_id"], s,
+                                    st.seed, 9, ex.shadow_eps, np.inf)
+                for l, lr in enumerate(r["lights"]):
+                    if lr is not None:
+                        blk, _ = _winner(oracle_lib, cloud, r["p"], lr[0], r["ray_id"], s, st.seed,
+                                         1 + l, ex.shadow_eps, lr[1])
+                        bits |= (blk < 0) << l
+            assert (cam_out, bounce, bits) == tuple(diag[i, s]), (v, p, s)
+    assert n_ground > 20
+    # a planted mistake: a sample's camera hit replaced by an unrelated id
+    i = next(i for i in range(len(items)) if diag[i, 0, 0] >= 0)
+    wrong = diag[i, 0].copy()
+    wrong[0] = (wrong[0] + 1234) % cloud.M
+    v, p = items[i]
+    k = _parity.classify_scene_sample(cloud, cams[v], ex, st, p, 0, wrong, diag[i, 0])
+    assert k == "other"
