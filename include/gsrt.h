@@ -171,8 +171,14 @@ typedef struct gs_bvh gs_bvh;
  *   GS_NODES_WIDE4_Q8  64-byte 4-wide nodes, child boxes quantised to 8 bits
  *                      per plane with outward rounding (a decoded box always
  *                      contains the FP32 box, so no hit is lost and every
- *                      result equals the FP32 traversal's) */
-enum { GS_NODES_BINARY = 0, GS_NODES_WIDE4 = 1, GS_NODES_WIDE4_Q8 = 2 };
+ *                      result equals the FP32 traversal's)
+ *   GS_NODES_BINARY_Q8 binary nodes as GS_NODES_BINARY, with the 8-, 16- and
+ *                      32-wide copies in 8-bit form: per wide node a 32-byte
+ *                      header (origin, power-of-two scale per axis), then 16
+ *                      bytes per child (six 8-bit planes rounded outward
+ *                      with one spare quantum, the reference); unless
+ *                      M > 2^24. Every result equals GS_NODES_BINARY's. */
+enum { GS_NODES_BINARY = 0, GS_NODES_WIDE4 = 1, GS_NODES_WIDE4_Q8 = 2, GS_NODES_BINARY_Q8 = 3 };
 
 typedef struct gs_build_options {
     int32_t node_format; /* GS_NODES_* */

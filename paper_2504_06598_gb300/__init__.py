@@ -69,8 +69,9 @@ class _BuildOptions(C.Structure):
     _fields_ = [("node_format", C.c_int32), ("reserved", C.c_int32 * 7)]
 
 
-NODES_BINARY, NODES_WIDE4, NODES_WIDE4_Q8 = 0, 1, 2
-NODE_FORMATS = {"binary": NODES_BINARY, "wide4": NODES_WIDE4, "wide4_q8": NODES_WIDE4_Q8}
+NODES_BINARY, NODES_WIDE4, NODES_WIDE4_Q8, NODES_BINARY_Q8 = 0, 1, 2, 3
+NODE_FORMATS = {"binary": NODES_BINARY, "wide4": NODES_WIDE4, "wide4_q8": NODES_WIDE4_Q8,
+                "binary_q8": NODES_BINARY_Q8}
 
 
 _lib = None

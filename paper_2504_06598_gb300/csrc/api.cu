@@ -126,7 +126,8 @@ gs_status gs_build_bvh_ex(const gs_gaussians *g, const gs_build_options *opt, gs
                           void *stream) {
     if (!out) return fail(GS_ERR_INVALID_ARG, "out is NULL");
     const int format = opt ? opt->node_format : GS_NODES_BINARY;
-    if (format != GS_NODES_BINARY && format != GS_NODES_WIDE4 && format != GS_NODES_WIDE4_Q8)
+    if (format != GS_NODES_BINARY && format != GS_NODES_WIDE4 && format != GS_NODES_WIDE4_Q8 &&
+        format != GS_NODES_BINARY_Q8)
         return fail(GS_ERR_INVALID_ARG, "node_format=%d unknown", format);
     if (opt)
         for (int i = 0; i < 7; ++i)
@@ -143,10 +144,14 @@ gs_status gs_build_bvh_ex(const gs_gaussians *g, const gs_build_options *opt, gs
     const int64_t nn = M > 1 ? M - 1 : 1;
     const int64_t tiles = radix_tiles(cap > 0 ? cap : 1);
     const int64_t scan_n = 256 * tiles > nn ? 256 * tiles : nn;
-    const bool wide = format != GS_NODES_BINARY;
+    const bool q8 = format == GS_NODES_BINARY_Q8;
+    const bool wide = format == GS_NODES_WIDE4 || format == GS_NODES_WIDE4_Q8;
     const size_t wide_bytes = format == GS_NODES_WIDE4 ? sizeof(Node4) : sizeof(NodeQ4);
-    // the W-wide records of the binary format; offsets must fit 26 bits
-    const int64_t recs = cap + nn;
+    // the W-wide records of the binary formats (at most one per leaf and
+    // one per internal node, plus two header units per wide node in the
+    // 8-bit form); offsets must fit 26 bits
+    const int64_t recs = q8 ? cap + 3 * nn : cap + nn;
+    const size_t rec_bytes = q8 ? sizeof(ChildQ8) : sizeof(ChildRec);
     const bool grouped = !wide && cap > 0 && recs <= (int64_t)kWideOffsetMask;
     b->node_format = format;
     struct Req { void **p; size_t bytes; } reqs[] = {
@@ -167,13 +172,13 @@ gs_status gs_build_bvh_ex(const gs_gaussians *g, const gs_build_options *opt, gs
         {(void **)&b->depth, wide ? (size_t)nn * 4 : 0},
         {(void **)&b->wmap, wide ? (size_t)nn * 4 : 0},
         {(void **)&b->node_depth, grouped ? (size_t)nn * 4 : 0},
-        {(void **)&b->group[0].rec, grouped ? (size_t)recs * sizeof(ChildRec) : 0},
+        {(void **)&b->group[0].rec, grouped ? (size_t)recs * rec_bytes : 0},
         {(void **)&b->group[0].cnt, grouped ? (size_t)nn * 4 : 0},
         {(void **)&b->group[0].off, grouped ? (size_t)nn * 4 : 0},
-        {(void **)&b->group[1].rec, grouped ? (size_t)recs * sizeof(ChildRec) : 0},
+        {(void **)&b->group[1].rec, grouped ? (size_t)recs * rec_bytes : 0},
         {(void **)&b->group[1].cnt, grouped ? (size_t)nn * 4 : 0},
         {(void **)&b->group[1].off, grouped ? (size_t)nn * 4 : 0},
-        {(void **)&b->group[2].rec, grouped ? (size_t)recs * sizeof(ChildRec) : 0},
+        {(void **)&b->group[2].rec, grouped ? (size_t)recs * rec_bytes : 0},
         {(void **)&b->group[2].cnt, grouped ? (size_t)nn * 4 : 0},
         {(void **)&b->group[2].off, grouped ? (size_t)nn * 4 : 0},
     };
@@ -240,7 +245,8 @@ gs_status gs_bvh_get_info(const gs_bvh *b, gs_bvh_info *info) {
 
 gs_status gs_bvh_export_wide(const gs_bvh *b, void *out, int64_t capacity, int64_t *n_out) {
     if (!b || !n_out) return fail(GS_ERR_INVALID_ARG, "NULL argument");
-    if (b->node_format == GS_NODES_BINARY) return fail(GS_ERR_INVALID_ARG, "handle has binary nodes");
+    if (b->node_format == GS_NODES_BINARY || b->node_format == GS_NODES_BINARY_Q8)
+        return fail(GS_ERR_INVALID_ARG, "handle has binary nodes");
     if (capacity < 0) return fail(GS_ERR_INVALID_ARG, "negative capacity");
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "synchronize");

@@ -269,7 +269,7 @@ __device__ void enumerate_packet(const TraceArgs &a, const Ray<N> &r, const floa
 // sum_k g . (c_i - c_k) over the slots the candidate is in front of; the
 // group's sum goes back to that lane, which chains it through alpha and
 // adds the gradients once for the group.
-template <int N, int LG>
+template <int N, int LG, bool Q8>
 __device__ void enumerate_group(const TraceArgs &a, const Ray<N> &r, const float ck[N][3],
                                 const float g[3], const float Y[16], uint32_t *s_ref, float *s_t,
                                 uint32_t &err) {
@@ -296,14 +296,7 @@ __device__ void enumerate_group(const TraceArgs &a, const Ray<N> &r, const float
         uint32_t ref = kEmpty;
         float te = INFINITY;
         bool hit = false;
-        if (sub < n_child) {
-            const float4 *cp =
-                reinterpret_cast<const float4 *>(a.grec + (node & kWideOffsetMask) + sub);
-            const float4 q0 = __ldg(cp), q1 = __ldg(cp + 1);
-            const float bx[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
-            ref = __float_as_uint(q1.z);
-            hit = slab(bx, r.inv, r.oinv, a.t_min, G, te);
-        }
+        if (sub < n_child) hit = group_child<Q8>(a.grec, node, sub, r.inv, r.oinv, a.t_min, G, ref, te);
         const bool leaf = (ref & kLeafBit) != 0u;
         if ((__ballot_sync(gmask, hit && leaf) >> base) & kLaneBits) {
             Cand c;
@@ -384,7 +377,7 @@ __device__ void enumerate_group(const TraceArgs &a, const Ray<N> &r, const float
 // LG: log2 of the lanes per pixel when the grouped traversals are used, else
 // 0. The grouped form is latency-bound and built for eight resident blocks
 // per SM; the per-lane form for three.
-template <int N, int LG>
+template <int N, int LG, bool Q8>
 __global__ void __launch_bounds__(kThreads, LG >= 3 ? kGroupMinBlocks : 3) k_backward(const TraceArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;
@@ -442,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, LG >= 3 ? kGroupMinBlocks : 3) k_bac
             if (a.n_nodes == 0) continue;
             // 1) the forward traversal: same keys, same winners
             if constexpr (LG >= 3)
-                traverse_group<N, false, LG>(a, r, pass, grp_ref, grp_t, err, cnt);
+                traverse_group<N, false, LG, false, Q8>(a, r, pass, grp_ref, grp_t, err, cnt);
             else
                 traverse_packet<N, false>(a, r, pass, stack, stack_t, err, cnt);
             // 2) colours of the winners; dLoss/dk of the selected Gaussians
@@ -479,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, LG >= 3 ? kGroupMinBlocks : 3) k_bac
             update_clip(r, a.t_max);
             if (!live) r.t_far = -INFINITY;
             if constexpr (LG >= 3)
-                enumerate_group<N, LG>(a, r, ck, g, Y, grp_ref, grp_t, err);
+                enumerate_group<N, LG, Q8>(a, r, ck, g, Y, grp_ref, grp_t, err);
             else
                 enumerate_packet<N>(a, r, ck, g, Y, stack, stack_t, err);
             __syncwarp();
@@ -488,13 +481,13 @@ __global__ void __launch_bounds__(kThreads, LG >= 3 ? kGroupMinBlocks : 3) k_bac
     if (err) atomicOr(a.status, err);
 }
 
-template <int N, int LG>
+template <int N, int LG, bool Q8>
 gs_status launch_backward_nl(const TraceArgs &a, cudaStream_t s) {
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_backward<N, LG>, kThreads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_backward<N, LG, Q8>, kThreads, 0);
     if (e != cudaSuccess) return cuda_fail(e, "backward launch setup");
     const int tw_lg = tile_w_log2(a.lpp_log2), th_lg = 5 - a.lpp_log2 - tw_lg;
     const uint32_t tiles = (uint32_t)(((a.width + (1 << tw_lg) - 1) >> tw_lg) *
@@ -504,22 +497,29 @@ gs_status launch_backward_nl(const TraceArgs &a, cudaStream_t s) {
     if (blocks > max_blocks) blocks = max_blocks;
     if ((e = cudaMemsetAsync(a.work, 0, sizeof(uint32_t), s)) != cudaSuccess)
         return cuda_fail(e, "reset work counter");
-    k_backward<N, LG><<<blocks, kThreads, 0, s>>>(a);
+    k_backward<N, LG, Q8><<<blocks, kThreads, 0, s>>>(a);
     return GS_OK;
 }
 
 // Groups of 8 or more lanes on one pixel use the wide copy of their width.
 template <int N>
 gs_status launch_backward_n(const TraceArgs &a, cudaStream_t s) {
-    if (a.grec != nullptr) {
+    if (a.grec != nullptr && a.gq8) {
         switch (a.lpp_log2) {
-            case 5: return launch_backward_nl<N, 5>(a, s);
-            case 4: return launch_backward_nl<N, 4>(a, s);
-            case 3: return launch_backward_nl<N, 3>(a, s);
+            case 5: return launch_backward_nl<N, 5, true>(a, s);
+            case 4: return launch_backward_nl<N, 4, true>(a, s);
+            case 3: return launch_backward_nl<N, 3, true>(a, s);
+            default: break;
+        }
+    } else if (a.grec != nullptr) {
+        switch (a.lpp_log2) {
+            case 5: return launch_backward_nl<N, 5, false>(a, s);
+            case 4: return launch_backward_nl<N, 4, false>(a, s);
+            case 3: return launch_backward_nl<N, 3, false>(a, s);
             default: break;
         }
     }
-    return launch_backward_nl<N, 0>(a, s);
+    return launch_backward_nl<N, 0, false>(a, s);
 }
 
 }  // namespace
@@ -560,6 +560,7 @@ gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinho
     if (b->node_depth && a.lpp_log2 >= 3) {
         a.grec = b->group[a.lpp_log2 - 3].rec;
         a.gcnt = b->group[a.lpp_log2 - 3].cnt;
+        a.gq8 = b->node_format == GS_NODES_BINARY_Q8;
     }
     a.d_rgb = d_rgb;
     a.log_scales = g->log_scales;

@@ -609,12 +609,13 @@ __device__ __forceinline__ uint32_t leaves_under(const Node &nd) {
 }
 
 // Children of the wide node at each binary internal node (0 where none);
-// the same count seeds the offsets.
+// the same count, plus `header` units where a node exists, seeds the
+// offsets.
 template <int LEVELS>
 __global__ void k_count_wide(int64_t n_int, const Node *__restrict__ nodes,
                              const uint32_t *__restrict__ depth,
                              const uint32_t *__restrict__ parent_int, uint32_t *__restrict__ cnt,
-                             uint32_t *__restrict__ off) {
+                             uint32_t *__restrict__ off, uint32_t header) {
     constexpr uint32_t W = 1u << LEVELS;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_int) return;
@@ -636,7 +637,7 @@ __global__ void k_count_wide(int64_t n_int, const Node *__restrict__ nodes,
         }
     }
     cnt[i] = c;
-    off[i] = c;
+    off[i] = c ? c + header : 0u;
 }
 
 // Writes the child records of every wide node at its offset.
@@ -673,6 +674,96 @@ __global__ void k_collapse_wide(int64_t n_int, const Node *__restrict__ nodes,
         c.reserved = 0;
         dst[j] = c;
     }
+}
+
+// 8-bit planes of one child box against its node's frame (origin, scale):
+// lower planes rounded down and upper planes rounded up, each by one more
+// quantum, so that the traversal's decoding (whose rounding stays under
+// half a quantum) still covers the FP32 box. A non-finite box is flagged.
+__device__ __forceinline__ void quant_child(const float b[6], const float origin[3],
+                                            const float scale[3], uint32_t &q0, uint32_t &q1) {
+    uint32_t lo[3], hi[3];
+    bool finite = true;
+    for (int a = 0; a < 3; ++a) finite = finite && isfinite(b[a]) && isfinite(b[3 + a]);
+    for (int a = 0; a < 3; ++a) {
+        float ql = floorf((b[a] - origin[a]) / scale[a]) - 1.0f;
+        float qh = ceilf((b[3 + a] - origin[a]) / scale[a]) + 1.0f;
+        // exact checks in the frame (q * scale is exact for a power-of-two
+        // scale): one quantum of room below lo and above hi
+        while (ql > 0.0f && !(__fadd_rn(origin[a], (ql + 1.0f) * scale[a]) <= b[a])) ql -= 1.0f;
+        while (qh < 255.0f && !(__fadd_rn(origin[a], (qh - 1.0f) * scale[a]) >= b[3 + a])) qh += 1.0f;
+        lo[a] = finite ? (uint32_t)fminf(fmaxf(ql, 0.0f), 255.0f) : 0u;
+        hi[a] = finite ? (uint32_t)fminf(fmaxf(qh, 0.0f), 255.0f) : 0u;
+    }
+    q0 = lo[0] | lo[1] << 8 | lo[2] << 16 | hi[0] << 24;
+    q1 = hi[1] | hi[2] << 8 | (finite ? 0u : kQ8Skip);
+}
+
+// Frame of an 8-bit wide node from the union of its children's boxes:
+// per axis a power-of-two scale with the extent plus two spare quanta
+// within 255 quanta, and the origin one quantum below the lower bound.
+__device__ __forceinline__ void quant_frame(const float lo[3], const float hi[3], float origin[3],
+                                            float scale[3]) {
+    for (int a = 0; a < 3; ++a) {
+        float l = lo[a], h = hi[a];
+        if (!(l <= h)) { l = 0.0f; h = 0.0f; }
+        const float ext = h - l;
+        int e = ext > 0.0f ? (int)ceilf(log2f(ext / 251.0f)) : -120;
+        e = max(e, -120);
+        while (251.0f * ldexpf(1.0f, e) < ext) ++e;
+        e = min(e, 120);
+        scale[a] = ldexpf(1.0f, e);
+        origin[a] = l - scale[a];
+    }
+}
+
+// Writes every wide node of the 8-bit form at its offset: the header from
+// the children's union box, then one unit per child.
+template <int LEVELS>
+__global__ void k_collapse_wide_q8(int64_t n_int, const Node *__restrict__ nodes,
+                                   const uint32_t *__restrict__ cnt,
+                                   const uint32_t *__restrict__ off,
+                                   const uint32_t *__restrict__ order,
+                                   const float *__restrict__ aabb, uint4 *__restrict__ units) {
+    constexpr uint32_t W = 1u << LEVELS;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int || cnt[i] == 0u) return;
+    uint4 *dst = units + off[i];
+    const Node ndi = nodes[i];
+    float ulo[3] = {INFINITY, INFINITY, INFINITY}, uhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float origin[3], scale[3];
+    if (leaves_under(ndi) <= W) {
+        for (uint32_t k = ndi.leaf_range[0]; k <= ndi.leaf_range[1]; ++k) {
+            const float *b = aabb + 6 * (int64_t)order[k];
+            for (int q = 0; q < 3; ++q) { ulo[q] = fminf(ulo[q], b[q]); uhi[q] = fmaxf(uhi[q], b[3 + q]); }
+        }
+        quant_frame(ulo, uhi, origin, scale);
+        uint32_t j = kGroupQHeaderUnits;
+        for (uint32_t k = ndi.leaf_range[0]; k <= ndi.leaf_range[1]; ++k, ++j) {
+            const float *b = aabb + 6 * (int64_t)order[k];
+            const float bx[6] = {b[0], b[1], b[2], b[3], b[4], b[5]};
+            uint32_t q0, q1;
+            quant_child(bx, origin, scale, q0, q1);
+            dst[j] = make_uint4(q0, q1, kLeafBit | k, 0u);
+        }
+    } else {
+        uint32_t ref[1 << LEVELS];
+        float box[1 << LEVELS][6];
+        const int n = expand_wide<LEVELS>(nodes, (uint32_t)i, ref, box);
+        for (int j = 0; j < n; ++j)
+            for (int q = 0; q < 3; ++q) { ulo[q] = fminf(ulo[q], box[j][q]); uhi[q] = fmaxf(uhi[q], box[j][3 + q]); }
+        quant_frame(ulo, uhi, origin, scale);
+        for (int j = 0; j < n; ++j) {
+            uint32_t q0, q1;
+            quant_child(box[j], origin, scale, q0, q1);
+            const uint32_t r = ref[j];
+            const uint32_t c = (r & kLeafBit) ? r : (((cnt[r] - 1u) << kWideCountShift) | off[r]);
+            dst[kGroupQHeaderUnits + j] = make_uint4(q0, q1, c, 0u);
+        }
+    }
+    dst[0] = make_uint4(__float_as_uint(origin[0]), __float_as_uint(origin[1]),
+                        __float_as_uint(origin[2]), __float_as_uint(scale[0]));
+    dst[1] = make_uint4(__float_as_uint(scale[1]), __float_as_uint(scale[2]), 0u, 0u);
 }
 
 inline unsigned grid_for(int64_t n, int threads) {
@@ -739,7 +830,7 @@ gs_status build_into(gs_bvh *b, const gs_gaussians *g, cudaStream_t s) {
                                                    g->opacity_logits, b->aabb, b->prims, b->nodes,
                                                    parent_int, parent_leaf, b->arrive);
     }
-    if (b->node_format != GS_NODES_BINARY) {
+    if (b->node_format == GS_NODES_WIDE4 || b->node_format == GS_NODES_WIDE4_Q8) {
         const int64_t n_int = b->n_nodes;
         if (M == 1) {
             if ((e = cudaMemsetAsync(b->depth, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "memset depth");
@@ -757,23 +848,37 @@ gs_status build_into(gs_bvh *b, const gs_gaussians *g, cudaStream_t s) {
     }
     if (b->node_depth) {
         const int64_t n_int = b->n_nodes;
+        const bool q8 = b->node_format == GS_NODES_BINARY_Q8;
+        const uint32_t hdr = q8 ? (uint32_t)kGroupQHeaderUnits : 0u;
         k_node_depth<<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->parent, b->node_depth);
         const GroupTree *t = b->group;
         k_count_wide<3><<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->nodes, b->node_depth, b->parent,
-                                                            t[0].cnt, t[0].off);
+                                                            t[0].cnt, t[0].off, hdr);
         scan_exclusive(t[0].off, n_int, b->scan_tmp, s);
-        k_collapse_wide<3><<<grid_for(n_int, 256), 256, 0, s>>>(n_int, b->nodes, t[0].cnt, t[0].off,
-                                                               order, b->aabb, t[0].rec);
+        if (q8)
+            k_collapse_wide_q8<3><<<grid_for(n_int, 256), 256, 0, s>>>(
+                n_int, b->nodes, t[0].cnt, t[0].off, order, b->aabb, static_cast<uint4 *>(t[0].rec));
+        else
+            k_collapse_wide<3><<<grid_for(n_int, 256), 256, 0, s>>>(
+                n_int, b->nodes, t[0].cnt, t[0].off, order, b->aabb, static_cast<ChildRec *>(t[0].rec));
         k_count_wide<4><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, b->node_depth, b->parent,
-                                                            t[1].cnt, t[1].off);
+                                                            t[1].cnt, t[1].off, hdr);
         scan_exclusive(t[1].off, n_int, b->scan_tmp, s);
-        k_collapse_wide<4><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, t[1].cnt, t[1].off,
-                                                               order, b->aabb, t[1].rec);
+        if (q8)
+            k_collapse_wide_q8<4><<<grid_for(n_int, 128), 128, 0, s>>>(
+                n_int, b->nodes, t[1].cnt, t[1].off, order, b->aabb, static_cast<uint4 *>(t[1].rec));
+        else
+            k_collapse_wide<4><<<grid_for(n_int, 128), 128, 0, s>>>(
+                n_int, b->nodes, t[1].cnt, t[1].off, order, b->aabb, static_cast<ChildRec *>(t[1].rec));
         k_count_wide<5><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, b->node_depth, b->parent,
-                                                            t[2].cnt, t[2].off);
+                                                            t[2].cnt, t[2].off, hdr);
         scan_exclusive(t[2].off, n_int, b->scan_tmp, s);
-        k_collapse_wide<5><<<grid_for(n_int, 128), 128, 0, s>>>(n_int, b->nodes, t[2].cnt, t[2].off,
-                                                               order, b->aabb, t[2].rec);
+        if (q8)
+            k_collapse_wide_q8<5><<<grid_for(n_int, 128), 128, 0, s>>>(
+                n_int, b->nodes, t[2].cnt, t[2].off, order, b->aabb, static_cast<uint4 *>(t[2].rec));
+        else
+            k_collapse_wide<5><<<grid_for(n_int, 128), 128, 0, s>>>(
+                n_int, b->nodes, t[2].cnt, t[2].off, order, b->aabb, static_cast<ChildRec *>(t[2].rec));
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "build launch");
     return GS_OK;

@@ -55,14 +55,38 @@ struct __align__(16) ChildRec {
     uint32_t reserved;
 };
 static_assert(sizeof(ChildRec) == 32, "ChildRec must be 32 bytes");
+// 8-bit form of the W-wide records (handles built with
+// GS_NODES_BINARY_Q8), in 16-byte units: a wide node is a two-unit header
+// (GroupQHeader) followed by one unit per child (ChildQ8). Plane q of axis
+// a of a child decodes to origin[a] + q * scale[a] (scale a power of two);
+// the build rounds lower planes down and upper planes up with one spare
+// quantum on each side, so the decoded box contains the child's FP32 box
+// with room for the traversal's rounding. An internal child is referenced
+// as (count - 1) << 26 | unit of its node's header.
+struct __align__(16) GroupQHeader {
+    float origin[3];
+    float scale[3];
+    uint32_t reserved[2];
+};
+static_assert(sizeof(GroupQHeader) == 32, "GroupQHeader must be 32 bytes");
+struct __align__(16) ChildQ8 {
+    uint32_t q0;     // qlo.x | qlo.y << 8 | qlo.z << 16 | qhi.x << 24
+    uint32_t q1;     // qhi.y | qhi.z << 8 | flags << 16 (bit 0: never entered)
+    uint32_t child;
+    uint32_t reserved;
+};
+static_assert(sizeof(ChildQ8) == 16, "ChildQ8 must be 16 bytes");
+constexpr int kGroupQHeaderUnits = 2;
+constexpr uint32_t kQ8Skip = 1u << 16;  // q1 flag: a child with a non-finite box
 constexpr int kWideCountShift = 26;
 constexpr uint32_t kWideOffsetMask = (1u << kWideCountShift) - 1u;
 constexpr int kGroupTrees = 3;  // W = 8 << i: collapses of 3, 4 and 5 binary levels
 
-// One W-wide hierarchy: records, and per binary internal node the child
-// count of the wide node there (0 where none) and its first record.
+// One W-wide hierarchy: records (ChildRec, or 16-byte units of the 8-bit
+// form), and per binary internal node the child count of the wide node
+// there (0 where none) and its first record or unit.
 struct GroupTree {
-    ChildRec *rec;
+    void *rec;
     uint32_t *cnt;
     uint32_t *off;
 };

@@ -37,10 +37,13 @@ namespace gsrt {
 namespace {
 
 // Template values of FMT for the cooperative traversal of the W-wide records
-// by groups of W = 8, 16, 32 lanes on one pixel (kFmtGroup + log2 W); the
-// others are GS_NODES_*.
+// by groups of W = 8, 16, 32 lanes on one pixel: kFmtGroup + log2 W for the
+// FP32 records, kFmtGroupQ8 + log2 W for the 8-bit ones; the others are
+// GS_NODES_*.
 constexpr int kFmtGroup = 8;
+constexpr int kFmtGroupQ8 = 16;
 __host__ __device__ constexpr bool is_group_fmt(int f) { return f >= kFmtGroup + 3; }
+__host__ __device__ constexpr bool is_group_q8(int f) { return f >= kFmtGroupQ8 + 3; }
 
 // Persistent kernel: each warp repeatedly takes the next tile (one atomic
 // per tile, so the tail of the launch stays balanced), then runs all passes
@@ -70,7 +73,7 @@ __global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? group_min_blocks
     unsigned long long n_shaded = 0, n_rays = 0;
     // group stacks: each warp's pool split evenly among its groups
     constexpr bool grouped = is_group_fmt(FMT);
-    constexpr int LG = grouped ? FMT - kFmtGroup : 3;
+    constexpr int LG = grouped ? (FMT & 7) : 3;
     __shared__ uint32_t s_ref[grouped ? kThreads / 32 : 1][grouped ? kGroupPool : 1];
     __shared__ float s_t[grouped ? kThreads / 32 : 1][grouped ? kGroupPool : 1];
     const int grp_off = grouped ? (lane >> LG) * (kGroupPool >> (5 - LG)) : 0;
@@ -112,7 +115,8 @@ __global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? group_min_blocks
             if (!live) r.t_far = -INFINITY;  // lanes off the image never hit
             if (a.n_nodes > 0) {
                 if constexpr (grouped)
-                    traverse_group<N, COUNT, LG, true>(a, r, pass, grp_ref, grp_t, err, cnt);
+                    traverse_group<N, COUNT, LG, true, is_group_q8(FMT)>(a, r, pass, grp_ref,
+                                                                          grp_t, err, cnt);
                 else if constexpr (FMT == GS_NODES_BINARY)
                     traverse_packet<N, COUNT>(a, r, pass, stack, stack_t, err, cnt);
                 else
@@ -202,6 +206,11 @@ gs_status launch_n(const TraceArgs &a, int format, bool count, cudaStream_t s) {
         if (a.lpp_log2 == 4) return launch_nf<N, kFmtGroup + 4>(a, count, s);
         if (a.lpp_log2 == 3) return launch_nf<N, kFmtGroup + 3>(a, count, s);
     }
+    if (format == GS_NODES_BINARY_Q8 && a.grec != nullptr) {
+        if (a.lpp_log2 == 5) return launch_nf<N, kFmtGroupQ8 + 5>(a, count, s);
+        if (a.lpp_log2 == 4) return launch_nf<N, kFmtGroupQ8 + 4>(a, count, s);
+        if (a.lpp_log2 == 3) return launch_nf<N, kFmtGroupQ8 + 3>(a, count, s);
+    }
     switch (format) {
         case GS_NODES_WIDE4: return launch_nf<N, GS_NODES_WIDE4>(a, count, s);
         case GS_NODES_WIDE4_Q8: return launch_nf<N, GS_NODES_WIDE4_Q8>(a, count, s);
@@ -238,7 +247,8 @@ void trace_layout(const gs_bvh *b, const gs_trace_params *p, int *S_out, int *sp
     *S_out = S;
     *spp_eff_out = (p->spp + S - 1) / S;
     *lpp_log2_out = lanes_per_pixel_log2(*spp_eff_out);
-    *grouped_out = b->node_format == GS_NODES_BINARY && b->node_depth && *lpp_log2_out >= 3;
+    *grouped_out = (b->node_format == GS_NODES_BINARY || b->node_format == GS_NODES_BINARY_Q8) &&
+                   b->node_depth && *lpp_log2_out >= 3;
 }
 
 gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
@@ -259,6 +269,7 @@ gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole 
         a.grec = nullptr;
         a.gcnt = nullptr;
     }
+    a.gq8 = b->node_format == GS_NODES_BINARY_Q8;
     a.prims = b->prims;
     a.sh = g->sh;
     a.n_nodes = b->n_nodes;

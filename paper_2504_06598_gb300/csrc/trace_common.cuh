@@ -19,8 +19,10 @@ constexpr int kThreads = 128;
 struct TraceArgs {
     const Node *nodes;
     const void *wide;  // Node4 or NodeQ4 when the handle has wide nodes
-    const ChildRec *grec;  // W-wide records for the launch's group size, or null
+    const void *grec;      // W-wide records (ChildRec, or the 8-bit units) for the
+                           // launch's group size, or null
     const uint32_t *gcnt;  // their per-node child counts (the root's at 0)
+    int gq8;               // 1 when grec holds the 8-bit form
     const PrimRec *prims;
     const void *sh;
     int64_t n_nodes;
@@ -786,6 +788,50 @@ __device__ __forceinline__ void traverse_lane(const TraceArgs &a, Ray<N> &r, int
 }
 
 // ---------------------------------------------------------------- groups
+// Child `sub` of the wide node `node` slab-tested against [t_min, G]: its
+// reference, its entry distance, and whether the ray enters its box. FP32
+// records hold the box. In the 8-bit form plane q of axis a lies at
+// origin + q * scale, i.e. at ray parameter q * A + B with A = scale * inv
+// and B = origin * inv - o * inv; q enters as the float 2^23 + q (exact, one
+// byte permute) and B as B - 2^23 A, rounded once (at most half a quantum of
+// the ray parameter, within the spare quantum the build leaves on each side).
+template <bool Q8>
+__device__ __forceinline__ bool group_child(const void *grec, uint32_t node, int sub,
+                                            const float inv[3], const float oinv[3], float t_min,
+                                            float G, uint32_t &ref, float &te) {
+    if constexpr (!Q8) {
+        const float4 *cp = reinterpret_cast<const float4 *>(
+            static_cast<const ChildRec *>(grec) + (node & kWideOffsetMask) + sub);
+        const float4 q0 = __ldg(cp), q1 = __ldg(cp + 1);
+        const float bx[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
+        ref = __float_as_uint(q1.z);
+        return slab(bx, inv, oinv, t_min, G, te);
+    } else {
+        const uint4 *u = static_cast<const uint4 *>(grec) + (node & kWideOffsetMask);
+        const float4 h0 = __ldg(reinterpret_cast<const float4 *>(u));
+        const float4 h1 = __ldg(reinterpret_cast<const float4 *>(u) + 1);
+        const uint4 c = __ldg(u + kGroupQHeaderUnits + sub);
+        ref = c.z;
+        const float A0 = h0.w * inv[0], A1 = h1.x * inv[1], A2 = h1.y * inv[2];
+        const float B0 = fmaf(-8388608.0f, A0, fmaf(h0.x, inv[0], -oinv[0]));
+        const float B1 = fmaf(-8388608.0f, A1, fmaf(h0.y, inv[1], -oinv[1]));
+        const float B2 = fmaf(-8388608.0f, A2, fmaf(h0.z, inv[2], -oinv[2]));
+        const float lx = __uint_as_float(__byte_perm(c.x, 0x4B000000u, 0x7440u));
+        const float ly = __uint_as_float(__byte_perm(c.x, 0x4B000000u, 0x7441u));
+        const float lz = __uint_as_float(__byte_perm(c.x, 0x4B000000u, 0x7442u));
+        const float hx = __uint_as_float(__byte_perm(c.x, 0x4B000000u, 0x7443u));
+        const float hy = __uint_as_float(__byte_perm(c.y, 0x4B000000u, 0x7440u));
+        const float hz = __uint_as_float(__byte_perm(c.y, 0x4B000000u, 0x7441u));
+        const float tx0 = fmaf(lx, A0, B0), tx1 = fmaf(hx, A0, B0);
+        const float ty0 = fmaf(ly, A1, B1), ty1 = fmaf(hy, A1, B1);
+        const float tz0 = fmaf(lz, A2, B2), tz1 = fmaf(hz, A2, B2);
+        const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), t_min));
+        const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), G));
+        te = tn;
+        return tn <= tf && !(c.y & kQ8Skip);
+    }
+}
+
 constexpr int kGroupPool = 512;    // stack entries per warp, split among its groups
 constexpr int kGroupMinBlocks = 8; // resident blocks per SM to build for
 
@@ -800,8 +846,8 @@ constexpr int kGroupMinBlocks = 8; // resident blocks per SM to build for
 // leaf a lane's own ray needs is visited, and each lane keeps its own slots
 // and clip, so per-lane results are those of an independent traversal.
 // POP2 selects the two-stage pop of the group stack (below); both pop the
-// same entries.
-template <int N, bool COUNT, int LG, bool POP2 = false>
+// same entries. Q8 reads the 8-bit form of the records.
+template <int N, bool COUNT, int LG, bool POP2 = false, bool Q8 = false>
 __device__ __forceinline__ void traverse_group(const TraceArgs &a, Ray<N> &r, int pass,
                                                uint32_t *s_ref, float *s_t, uint32_t &err,
                                                Counts &cnt) {
@@ -834,14 +880,7 @@ __device__ __forceinline__ void traverse_group(const TraceArgs &a, Ray<N> &r, in
         uint32_t ref = kEmpty;
         float te = INFINITY;
         bool hit = false;
-        if (sub < n_child) {
-            const float4 *cp =
-                reinterpret_cast<const float4 *>(a.grec + (node & kWideOffsetMask) + sub);
-            const float4 q0 = __ldg(cp), q1 = __ldg(cp + 1);
-            const float bx[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
-            ref = __float_as_uint(q1.z);
-            hit = slab(bx, r.inv, r.oinv, r.t_min, G, te);
-        }
+        if (sub < n_child) hit = group_child<Q8>(a.grec, node, sub, r.inv, r.oinv, r.t_min, G, ref, te);
         const bool leaf = (ref & kLeafBit) != 0u;
         const uint32_t lm = (__ballot_sync(gmask, hit && leaf) >> base) & kLaneBits;
         if (lm) {

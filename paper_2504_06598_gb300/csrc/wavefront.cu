@@ -124,7 +124,8 @@ __device__ __forceinline__ void trace_packet(const TraceArgs &a, Ray<1> &r, int 
                                              uint32_t *stack, float *stack_t, uint32_t &err,
                                              Counts &cnt) {
     if (a.n_nodes == 0) return;
-    if (FMT == GS_NODES_BINARY) traverse_packet<1, COUNT>(a, r, pass, stack, stack_t, err, cnt);
+    if constexpr (FMT == GS_NODES_BINARY || FMT == GS_NODES_BINARY_Q8)
+        traverse_packet<1, COUNT>(a, r, pass, stack, stack_t, err, cnt);
     else traverse_packet_wide<1, COUNT, FMT>(a, r, pass, stack, stack_t, err, cnt);
 }
 
@@ -135,7 +136,8 @@ __device__ __forceinline__ void trace_own_ray(const TraceArgs &a, Ray<1> &r, int
                                               uint32_t *stack, float *stack_t, uint32_t &err,
                                               Counts &cnt) {
     if (a.n_nodes == 0) return;
-    if (FMT == GS_NODES_BINARY) traverse_lane<1, COUNT>(a, r, pass, stack, stack_t, err, cnt);
+    if constexpr (FMT == GS_NODES_BINARY || FMT == GS_NODES_BINARY_Q8)
+        traverse_lane<1, COUNT>(a, r, pass, stack, stack_t, err, cnt);
     else traverse_packet_wide<1, COUNT, FMT>(a, r, pass, stack, stack_t, err, cnt);
 }
 
@@ -146,7 +148,9 @@ __device__ __forceinline__ void trace_pixel_ray(const TraceArgs &a, Ray<1> &r, i
                                                 uint32_t *stack, float *stack_t, uint32_t *g_ref,
                                                 float *g_t, uint32_t &err, Counts &cnt) {
     if (a.n_nodes == 0) return;
-    if constexpr (GLG >= 3) traverse_group<1, COUNT, GLG>(a, r, pass, g_ref, g_t, err, cnt);
+    if constexpr (GLG >= 3)
+        traverse_group<1, COUNT, GLG, false, FMT == GS_NODES_BINARY_Q8>(a, r, pass, g_ref, g_t, err,
+                                                                        cnt);
     else trace_packet<FMT, COUNT>(a, r, pass, stack, stack_t, err, cnt);
 }
 
@@ -528,6 +532,22 @@ gs_status launch_views_f<GS_NODES_BINARY>(const WaveArgs &w, int threads, int st
     return launch_views_g<GS_NODES_BINARY, 0>(w, threads, stack, s);
 }
 
+// Binary handles with 8-bit wide copies: the groups read the 8-bit records;
+// everything else is the binary form's.
+template <>
+gs_status launch_views_f<GS_NODES_BINARY_Q8>(const WaveArgs &w, int threads, int stack,
+                                             cudaStream_t s) {
+    if (w.t.grec != nullptr) {
+        switch (w.t.lpp_log2) {
+            case 5: return launch_views_g<GS_NODES_BINARY_Q8, 5>(w, threads, stack, s);
+            case 4: return launch_views_g<GS_NODES_BINARY_Q8, 4>(w, threads, stack, s);
+            case 3: return launch_views_g<GS_NODES_BINARY_Q8, 3>(w, threads, stack, s);
+            default: break;
+        }
+    }
+    return launch_views_g<GS_NODES_BINARY, 0>(w, threads, stack, s);
+}
+
 }  // namespace
 
 int64_t wave_slots(const gs_pinhole *cams, int n_views, const gs_scene_extras *ex,
@@ -607,6 +627,7 @@ gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_p
     if (b->node_depth && a.lpp_log2 >= 3) {
         a.grec = b->group[a.lpp_log2 - 3].rec;
         a.gcnt = b->group[a.lpp_log2 - 3].cnt;
+        a.gq8 = b->node_format == GS_NODES_BINARY_Q8;
     }
     const int tw_lg = tile_w_log2(a.lpp_log2), th_lg = 5 - a.lpp_log2 - tw_lg;
     uint32_t tiles = 0;
@@ -665,6 +686,7 @@ gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_p
     switch (b->node_format) {
         case GS_NODES_WIDE4: st = launch_views_f<GS_NODES_WIDE4>(w, threads, stack, s); break;
         case GS_NODES_WIDE4_Q8: st = launch_views_f<GS_NODES_WIDE4_Q8>(w, threads, stack, s); break;
+        case GS_NODES_BINARY_Q8: st = launch_views_f<GS_NODES_BINARY_Q8>(w, threads, stack, s); break;
         default: st = launch_views_f<GS_NODES_BINARY>(w, threads, stack, s); break;
     }
     if (st != GS_OK) return st;

@@ -37,9 +37,9 @@ def _cluster(seed=0, M=60, sh_degree=1):
                                 sh_degree)
 
 
-def _gpu_grads(gs, cloud, cam, d_rgb, **opts):
+def _gpu_grads(gs, cloud, cam, d_rgb, node_format="binary", **opts):
     g = gs.Gaussians.from_cloud(cloud)
-    bvh = gs.build_bvh(g)
+    bvh = gs.build_bvh(g, node_format=node_format)
     d = torch.from_numpy(np.ascontiguousarray(d_rgb, np.float32)).cuda().reshape(cam.height, cam.width, 3)
     grads = gs.trace_backward(bvh, g, cam, d, **opts)
     bvh.sync_status()
@@ -152,5 +152,23 @@ def test_grouped_and_packet_gradients_agree(gs):
     b = _gpu_grads(gs, cloud, cam, d_rgb, seed=2, spp=2, n_hits=8)
     for k in KEYS:
         scale = np.abs(b[k]).max()
+        assert scale > 0, k
+        assert np.abs(a[k] - b[k]).max() <= 1e-5 * scale, k
+
+
+@pytest.mark.parametrize("spp,n_hits", [(16, 1), (8, 4), (32, 1)])
+def test_binary_q8_gradients_match_binary(gs, spp, n_hits):
+    """The grouped backward on the 8-bit wide copies re-traces the same hits
+    and enumerates the same Gaussians: gradients equal the FP32 copies' up
+    to the order of the atomic float sums."""
+    cloud = scenes.shell_cloud(8, M=20000)
+    cam = scenes.default_camera(48, 36)
+    rng = np.random.default_rng(6)
+    d_rgb = rng.normal(size=(cam.width * cam.height, 3))
+    a = _gpu_grads(gs, cloud, cam, d_rgb, seed=2, spp=spp, n_hits=n_hits)
+    b = _gpu_grads(gs, cloud, cam, d_rgb, node_format="binary_q8", seed=2, spp=spp,
+                   n_hits=n_hits)
+    for k in KEYS:
+        scale = np.abs(a[k]).max()
         assert scale > 0, k
         assert np.abs(a[k] - b[k]).max() <= 1e-5 * scale, k

@@ -121,10 +121,12 @@ def test_stack_overflow_is_reported_then_cleared(gs):
     b = gs.trace_stochastic(bvh, g, cam, spp=2, stack_depth=48).cpu()
     bvh.sync_status()
     assert torch.equal(a, b)
-    # the grouped traversal (spp >= 8) keeps its own 128-entry group stacks
-    c = gs.trace_stochastic(bvh, g, cam, spp=8, stack_depth=1).cpu()
+    # the grouped traversal (8 or more lanes on a pixel) keeps its own group
+    # stacks in shared memory
+    assert gs.trace_layout(bvh, spp=8, samples_per_lane=1)["grouped"]
+    c = gs.trace_stochastic(bvh, g, cam, spp=8, stack_depth=1, samples_per_lane=1).cpu()
     bvh.sync_status()
-    d = gs.trace_stochastic(bvh, g, cam, spp=8, stack_depth=0).cpu()
+    d = gs.trace_stochastic(bvh, g, cam, spp=8, stack_depth=0, samples_per_lane=1).cpu()
     bvh.sync_status()
     assert torch.equal(c, d)
     bvh.free()

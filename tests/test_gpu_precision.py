@@ -1,8 +1,9 @@
 """Precision form: 4-wide hierarchies with FP32 and 8-bit quantised child
-boxes give exactly the FP32 binary traversal's samples (conservative boxes
-only prune), decoded 8-bit boxes contain the FP32 boxes, and SH stored in
-FP16 / BF16 shades within 1e-5 of the FP64 oracle fed the same rounded
-coefficients."""
+boxes, and the 8-bit form of the 8/16/32-wide copies that groups of lanes
+traverse, give exactly the FP32 binary traversal's samples (conservative
+boxes only prune), decoded 8-bit boxes contain the FP32 boxes, and SH
+stored in FP16 / BF16 shades within 1e-5 of the FP64 oracle fed the same
+rounded coefficients."""
 import numpy as np
 import pytest
 
@@ -54,6 +55,51 @@ def test_wide_formats_match_binary(gs, which, n_hits, spp):
         got = _trace(gs, g, cam, fmt, seed=3, spp=spp, n_hits=n_hits)
         for a, b in zip(ref, got):
             assert np.array_equal(a, b), fmt
+
+
+# (n_hits, spp, samples per lane): 8-, 16- and 32-lane groups with one
+# sample per lane, then the library's own layouts (32 lanes x 2 samples at
+# spp 64, 16 lanes x 4 slots at N=4 spp 16, 4-lane packets at spp 16)
+@pytest.mark.parametrize("which", ["tiny", "shell", "one", "coincident"])
+@pytest.mark.parametrize("n_hits,spp,spl", [(1, 8, 1), (1, 16, 1), (1, 32, 1), (1, 64, 0),
+                                            (4, 16, 0), (1, 16, 0), (2, 8, 1)])
+def test_binary_q8_groups_match_binary(gs, which, n_hits, spp, spl):
+    if which == "tiny":
+        cloud, cam = scenes.tiny_cloud(0), scenes.default_camera(40, 30)
+    elif which == "shell":
+        cloud, cam = scenes.shell_cloud(1, M=50000), scenes.default_camera(72, 40)
+    elif which == "one":
+        cloud, cam = scenes.tiny_cloud(2, M=1), scenes.default_camera(16, 16)
+        cloud.means[:] = 0.0
+        cloud.log_scales[:] = -1.0
+    else:
+        cloud, cam = scenes.tiny_cloud(3, M=700), scenes.default_camera(24, 24)
+        cloud.means[:] = 0.02
+        cloud.log_scales[:] += 1.5
+    g = gs.Gaussians.from_cloud(cloud)
+    kw = dict(seed=3, spp=spp, n_hits=n_hits, samples_per_lane=spl)
+    ref = _trace(gs, g, cam, "binary", **kw)
+    got = _trace(gs, g, cam, "binary_q8", **kw)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+
+
+def test_binary_q8_full_size_3m(gs):
+    """3M-Gaussian shell, 1080p, N=1 spp 64 (the precision form's launch):
+    every sample's hit and depth from the 8-bit 32-wide records equals the
+    FP32 records'; the image is bit-identical."""
+    cloud = scenes.shell_cloud(0, M=3_000_000)
+    cam = scenes.default_camera(1920, 1080)
+    g = gs.Gaussians.from_cloud(cloud, sh_dtype=torch.float16)
+    out = {}
+    for fmt in ("binary", "binary_q8"):
+        bvh = gs.build_bvh(g, node_format=fmt)
+        out[fmt] = gs.trace_stochastic(bvh, g, cam, seed=0, spp=64, want_hits=True)
+        bvh.sync_status()
+        bvh.free()
+    for a, b in zip(out["binary"], out["binary_q8"]):
+        assert torch.equal(a, b)
+    assert (out["binary"][1] >= 0).float().mean().item() > 0.05
 
 
 def _decode_q8(words):

@@ -37,8 +37,8 @@ def _run(gs, cloud, cam, spp, n_hits, seed=0, **kw):
     return out, ids, ts
 
 
-def _assert_parity(gs, cloud, cam, spp, n_hits, seed=0, pixels=None):
-    rgb, ids, ts = _run(gs, cloud, cam, spp, n_hits, seed)
+def _assert_parity(gs, cloud, cam, spp, n_hits, seed=0, pixels=None, **kw):
+    rgb, ids, ts = _run(gs, cloud, cam, spp, n_hits, seed, **kw)
     if pixels is None:
         pixels = np.arange(cam.width * cam.height)
     ref = oracle.render_pinhole(cloud, cam, scenes.TraceSettings(seed=seed, spp=spp, n_hits=n_hits),
@@ -60,15 +60,18 @@ def colour_ok(g, r, same):
     return True
 
 
-# spp picks the lanes per pixel (largest power of two <= spp, at most 32):
-# 1, 16, 4, 2 and 2 lanes here; 5 and 40 end on a partial round of samples.
-# spp = 8 or more runs the grouped 8-wide traversal, (8, 8) with eight slots.
+# With one sample per lane (spl 1) spp picks the lanes per pixel (largest
+# power of two <= spp, at most 32): 1, 16, 4, 2 and 2 lanes here; 5 and 40
+# end on a partial round of samples; 8 or more lanes run the grouped
+# traversal, (8, 8) with eight slots. spl 0 is the library's own choice of
+# samples per lane (unused slots past the last sample at spp 3, 5, 40).
+@pytest.mark.parametrize("spl", [0, 1])
 @pytest.mark.parametrize("spp,n_hits", [(1, 1), (16, 1), (4, 4), (2, 8), (3, 2), (5, 1), (40, 1),
                                         (8, 8)])
-def test_tiny_parity(gs, spp, n_hits):
+def test_tiny_parity(gs, spp, n_hits, spl):
     cloud = scenes.tiny_cloud(0)
     cam = scenes.default_camera(64, 64)
-    _assert_parity(gs, cloud, cam, spp, n_hits)
+    _assert_parity(gs, cloud, cam, spp, n_hits, samples_per_lane=spl)
 
 
 def test_shell_small_ragged(gs):
@@ -103,9 +106,9 @@ def test_grouped_and_packet_traversals_agree(gs):
     (per-lane packets): identical hits and depths."""
     cloud = scenes.shell_cloud(5, M=20000)
     cam = scenes.default_camera(56, 40)
-    _, a, ta = _run(gs, cloud, cam, spp=32, n_hits=1, seed=4)
-    _, b, tb = _run(gs, cloud, cam, spp=16, n_hits=2, seed=4)
-    _, c, tc = _run(gs, cloud, cam, spp=4, n_hits=8, seed=4)
+    _, a, ta = _run(gs, cloud, cam, spp=32, n_hits=1, seed=4, samples_per_lane=1)
+    _, b, tb = _run(gs, cloud, cam, spp=16, n_hits=2, seed=4, samples_per_lane=1)
+    _, c, tc = _run(gs, cloud, cam, spp=4, n_hits=8, seed=4, samples_per_lane=1)
     assert np.array_equal(a, b) and np.array_equal(a, c)
     assert np.array_equal(ta, tb) and np.array_equal(ta, tc)
 

@@ -79,7 +79,7 @@ def test_formats_and_launch_shapes_agree(gs, spp):
     cloud, cams, ex = _setup()
     g = gs.Gaussians.from_cloud(cloud)
     results = []
-    for fmt in ("binary", "wide4", "wide4_q8"):
+    for fmt in ("binary", "wide4", "wide4_q8", "binary_q8"):
         bvh = gs.build_bvh(g, node_format=fmt)
         for block, stack in ((128, 96), (64, 48), (256, 96)):
             rgb, smp = gs.render_views(bvh, g, cams, ex, seed=1, spp=spp, block_threads=block,
