@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the 3M-Gaussian precision-form record of the default run")
     ap.add_argument("--ref-pixels", type=int, default=512,
                     help="pixels per step of the reference (oracle) arm")
     ap.add_argument("--case", choices=["trace-1080p", "wavefront-4v", "backward-1080p"], default=None,
@@ -195,44 +197,34 @@ def run_backward(args):
     print(json.dumps(out), flush=True)
 
 
-def run_precision(args):
-    """Precision form: 3M-Gaussian shell (same generator), 1080p, N=1, 64 spp.
-    Every form is timed (hierarchy rebuild + trace, CUDA events, L2 flushed
-    between steps) and compared with the FP32 binary plain form (per-pixel
-    error) and with the FP64 oracle's exact blend on a 4,096-pixel subset."""
+PRECISION_M = 3_000_000
+# (name, SH storage dtype, node format); the first is the plain FP32 form
+PRECISION_FORMS = [("fp32-binary", "float32", "binary"), ("fp16-binary_q8", "float16", "binary_q8"),
+                   ("bf16-binary_q8", "bfloat16", "binary_q8"), ("fp16-binary", "float16", "binary"),
+                   ("fp32-wide4", "float32", "wide4"), ("fp16-wide4q8", "float16", "wide4_q8"),
+                   ("bf16-wide4q8", "bfloat16", "wide4_q8")]
+
+
+def precision_forms(gs, cloud, forms, steps, warmup, pixels, blend, flush):
+    """Time each precision form on the 1080p view at N=1 spp=64 (hierarchy
+    rebuild + trace per step, CUDA events, L2 flushed between steps) and
+    compare its image with the first form's (per-pixel) and with the exact
+    blend on the pixel subset."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2504_06598_gb300 as gs
-    import oracle
-    import scenes
-    M = 3_000_000
-    cloud = scenes.shell_cloud(0, M=M)
     cam = gs.Camera(W_IMG, H_IMG)
     npix = W_IMG * H_IMG
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    forms = [("fp32-binary", torch.float32, "binary"), ("fp16-binary", torch.float16, "binary"),
-             ("bf16-binary", torch.bfloat16, "binary"), ("fp32-wide4", torch.float32, "wide4"),
-             ("fp16-wide4q8", torch.float16, "wide4_q8"), ("bf16-wide4q8", torch.bfloat16, "wide4_q8")]
-    pix = scenes.pixel_subset(W_IMG, H_IMG, 4096)
-    t0 = time.perf_counter()
-    ref = oracle.render_pinhole(cloud, scenes.default_camera(W_IMG, H_IMG),
-                                scenes.TraceSettings(seed=0, spp=1), pixels=pix, want_hits=False)
-    oracle_s = time.perf_counter() - t0
-    out = {"metric": "precision form: Mrays/s and error at 3M Gaussians 1080p N=1 spp=64",
-           "workload": "shell-3M-1080p", "gaussians": M, "spp": SPP_N1, "n_hits": 1,
-           "oracle_subset_pixels": len(pix), "oracle_seconds": oracle_s, "forms": {}}
+    out = {}
     base_img = None
     for name, dt, fmt in forms:
-        g = gs.Gaussians.from_cloud(cloud, sh_dtype=dt)
+        g = gs.Gaussians.from_cloud(cloud, sh_dtype=getattr(torch, dt))
         bvh = gs.build_bvh(g, node_format=fmt)
         rgb = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32, device="cuda")
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             bvh.rebuild(g)
             gs.trace_stochastic(bvh, g, cam, seed=0, spp=SPP_N1, out=rgb)
         torch.cuda.synchronize()
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-        for k in range(args.steps):
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        for k in range(steps):
             flush.fill_(float(k))
             evs[k][0].record()
             bvh.rebuild(g)
@@ -242,25 +234,62 @@ def run_precision(args):
         torch.cuda.synchronize()
         bvh.sync_status()
         info = bvh.info()
+        lay = gs.trace_layout(bvh, spp=SPP_N1, n_hits=1)
         bvh.free()
         build = float(np.mean([a.elapsed_time(b) for a, b, _ in evs]))
         trace = float(np.mean([b.elapsed_time(c) for _, b, c in evs]))
         img = rgb.cpu().numpy().reshape(-1, 3).astype(np.float64)
         if base_img is None:
             base_img = img
-        sub = img[pix]
-        out["forms"][name] = {
-            "node_format": fmt, "sh_dtype": str(dt).replace("torch.", ""),
+        sub = img[pixels]
+        out[name] = {
+            "node_format": fmt, "sh_dtype": dt,
             "node_bytes": info["wide_node_bytes"] or info["node_bytes"],
-            "sh_bytes_per_gaussian": 48 * (4 if dt == torch.float32 else 2),
+            "group_record_bytes": {"binary": 32, "binary_q8": 16}.get(fmt),
+            "sh_bytes_per_gaussian": 48 * (4 if dt == "float32" else 2),
+            "grouped": lay["grouped"],
             "build_ms": build, "trace_ms": trace,
             "mrays_per_s": npix * SPP_N1 / ((build + trace) * 1e-3) / 1e6,
-            "rmse_vs_blend": float(np.sqrt(np.mean((sub - ref["blend"]) ** 2))),
-            "max_abs_vs_fp32_binary": float(np.abs(img - base_img).max()),
-            "rmse_vs_fp32_binary": float(np.sqrt(np.mean((img - base_img) ** 2))),
+            "rmse_vs_blend": float(np.sqrt(np.mean((sub - blend) ** 2))),
+            "max_abs_vs_" + forms[0][0]: float(np.abs(img - base_img).max()),
+            "rmse_vs_" + forms[0][0]: float(np.sqrt(np.mean((img - base_img) ** 2))),
         }
         del g
         torch.cuda.empty_cache()
+    return out
+
+
+def precision_blend(cloud, n_pix):
+    """The FP64 oracle's exact blend on a fixed seeded pixel subset."""
+    import oracle
+    import scenes
+    oracle.build()
+    pix = scenes.pixel_subset(W_IMG, H_IMG, n_pix)
+    t0 = time.perf_counter()
+    ref = oracle.render_pinhole(cloud, scenes.default_camera(W_IMG, H_IMG),
+                                scenes.TraceSettings(seed=0, spp=1), pixels=pix, want_hits=False)
+    return pix, ref["blend"], time.perf_counter() - t0
+
+
+def run_precision(args):
+    """Precision form: 3M-Gaussian shell (same generator), 1080p, N=1, 64 spp:
+    FP32 SH with the FP32 wide copies (the plain form), FP16/BF16 SH with the
+    8-bit wide copies, and the 4-wide FP32 / 8-bit per-lane forms; per-pixel
+    error against the plain form and RMSE against the FP64 oracle's exact
+    blend on a 4,096-pixel subset."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_06598_gb300 as gs
+    import scenes
+    cloud = scenes.shell_cloud(0, M=PRECISION_M)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    pix, blend, oracle_s = precision_blend(cloud, 4096)
+    out = {"metric": "precision form: Mrays/s and error at 3M Gaussians 1080p N=1 spp=64",
+           "workload": "shell-3M-1080p", "gaussians": PRECISION_M, "spp": SPP_N1, "n_hits": 1,
+           "oracle_subset_pixels": len(pix), "oracle_seconds": oracle_s,
+           "forms": precision_forms(gs, cloud, PRECISION_FORMS, args.steps, args.warmup, pix,
+                                    blend, flush)}
     print(json.dumps(out), flush=True)
 
 
@@ -792,6 +821,16 @@ def main():
                    "trace_ms_est": t4_per_spp * spp_eq},
             "oracle_estimator_n1": {"rmse": rmse(ref["est"])},
         }
+    if rank == 0 and not args.no_precision:
+        # the precision form beside the plain form (3M Gaussians, N=1 spp 64)
+        pcloud = scenes.shell_cloud(0, M=PRECISION_M)
+        ppix, pblend, pos = precision_blend(pcloud, 1024)
+        forms = precision_forms(gs, pcloud, PRECISION_FORMS[:2], min(args.steps, 5), args.warmup,
+                                ppix, pblend, flush)
+        line["precision_3m"] = {"gaussians": PRECISION_M, "spp": SPP_N1, "n_hits": 1,
+                                "rmse_pixels": len(ppix), "oracle_seconds": pos,
+                                "forms": forms}
+        del pcloud
     if rank == 0:
         print(json.dumps(line), flush=True)
     bvh.free()

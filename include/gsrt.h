@@ -122,7 +122,8 @@ typedef struct gs_pinhole {
  *                 not reproducible bit for bit)
  *   samples_per_lane
  *                 how many consecutive samples one lane of a traversal
- *                 carries (gs_trace_stochastic only): 1, 2, 4 or 8 with
+ *                 carries (gs_trace_stochastic and gs_trace_backward,
+ *                 each with its own choice for 0): 1, 2, 4 or 8 with
  *                 n_hits * samples_per_lane <= 8, or 0 to let the library
  *                 choose. The pixel then takes ceil(spp / S) passes, each
  *                 with n_hits * S slots (samples pass*n_hits*S + k),

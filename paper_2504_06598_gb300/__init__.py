@@ -347,7 +347,7 @@ def probe_copy(src, dst, repeats=1, stream=None):
 
 def trace_backward(bvh: Bvh, g: Gaussians, cam, d_rgb, seed=0, spp=1, n_hits=1, t_min=0.0,
                    t_max=float("inf"), bg=(0.0, 0.0, 0.0), stack_depth=0, stream_tag=0,
-                   grads=None, stream=None):
+                   grads=None, stream=None, samples_per_lane=0):
     """``gs_trace_backward``: stochastic gradients of sum(d_rgb * rgb).
 
     Returns (and accumulates into, if given) a dict of float32 gradients
@@ -362,7 +362,8 @@ def trace_backward(bvh: Bvh, g: Gaussians, cam, d_rgb, seed=0, spp=1, n_hits=1, 
     d_rgb = d_rgb.to(device=dev, dtype=torch.float32).contiguous()
     gs_ = g.struct()
     cs = cam.struct()
-    ps = _params(seed, spp, n_hits, t_min, t_max, bg, stack_depth, stream_tag, None)
+    ps = _params(seed, spp, n_hits, t_min, t_max, bg, stack_depth, stream_tag, None,
+                 samples_per_lane=samples_per_lane)
     _check(lib().gs_trace_backward(
         bvh.handle, C.byref(gs_), C.byref(cs), C.byref(ps), C.c_void_p(d_rgb.data_ptr()),
         C.c_void_p(grads["means"].data_ptr()), C.c_void_p(grads["log_scales"].data_ptr()),

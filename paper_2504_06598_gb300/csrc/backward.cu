@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kThreads, LG >= 3 ? kGroupMinBlocks : 3) k_bac
         r.any_hit = false;
         float Y[16];
         sh_basis(a.sh_degree, r.d, Y);
-        const float inv_s = 1.0f / (float)((int64_t)a.spp * N);
+        const float inv_s = 1.0f / (float)a.n_samples;
         float g[3] = {0.0f, 0.0f, 0.0f};
         if (valid)
             for (int ch = 0; ch < 3; ++ch) g[ch] = a.d_rgb[3 * pix + ch] * inv_s;
@@ -428,8 +428,12 @@ __global__ void __launch_bounds__(kThreads, LG >= 3 ? kGroupMinBlocks : 3) k_bac
         for (int j = 0; j < n_rounds; ++j) {
             const int pass = (j << lg) + sub;
             const bool live = valid && pass < a.spp;
+            // unused slots (sample index past the pixel's count) at -inf:
+            // nothing is in front of them and they never set the clip
 #pragma unroll
-            for (int k = 0; k < N; ++k) r.slot[k] = Slot{INFINITY, INFINITY, 0.0f, 0xffffffffu};
+            for (int k = 0; k < N; ++k)
+                r.slot[k] = pass * N + k < a.n_samples ? Slot{INFINITY, INFINITY, 0.0f, 0xffffffffu}
+                                                       : Slot{-INFINITY, -INFINITY, 0.0f, 0xffffffffu};
             update_clip(r, a.t_max);
             if (!live) r.t_far = -INFINITY;
             if (a.n_nodes == 0) continue;
@@ -524,10 +528,24 @@ gs_status launch_backward_n(const TraceArgs &a, cudaStream_t s) {
 
 }  // namespace
 
+// Samples one lane of the gradient launch carries when the caller leaves
+// the choice to the library (samples_per_lane = 0).
+static int auto_backward_samples_per_lane(int spp, int n_hits) {
+    (void)spp;
+    (void)n_hits;
+    return 1;
+}
+
 gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
                           const gs_trace_params *p, const float *d_rgb, float *d_means,
                           float *d_log_scales, float *d_quats, float *d_logits, float *d_sh,
                           cudaStream_t s) {
+    // a lane carries S consecutive samples: ceil(spp / S) passes of
+    // n_hits * S slots, the same sample indices and keys as the forward
+    int S = p->samples_per_lane > 0 ? p->samples_per_lane
+                                    : auto_backward_samples_per_lane(p->spp, p->n_hits);
+    while (S > 1 && S > p->spp) S >>= 1;
+    const int spp_eff = (p->spp + S - 1) / S;
     TraceArgs a = {};
     a.nodes = b->nodes;
     a.prims = b->prims;
@@ -548,7 +566,7 @@ gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinho
     a.key0 = (uint32_t)(p->seed & 0xffffffffu);
     a.key1 = (uint32_t)(p->seed >> 32);
     a.stream_tag = p->stream_tag;
-    a.spp = p->spp;
+    a.spp = spp_eff;
     a.n_samples = p->spp * p->n_hits;
     a.t_min = p->t_min;
     a.t_max = p->t_max;
@@ -556,7 +574,7 @@ gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinho
     a.step_limit = (uint32_t)(b->n_nodes + 8 < (int64_t)kStepLimit ? b->n_nodes + 8 : kStepLimit);
     a.status = b->status;
     a.work = b->status + 1;
-    a.lpp_log2 = lanes_per_pixel_log2(p->spp);
+    a.lpp_log2 = lanes_per_pixel_log2(spp_eff);
     if (b->node_depth && a.lpp_log2 >= 3) {
         a.grec = b->group[a.lpp_log2 - 3].rec;
         a.gcnt = b->group[a.lpp_log2 - 3].cnt;
@@ -571,7 +589,7 @@ gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinho
     a.g_logits = d_logits;
     a.g_sh = d_sh;
     gs_status st;
-    switch (p->n_hits) {
+    switch (p->n_hits * S) {
         case 1: st = launch_backward_n<1>(a, s); break;
         case 2: st = launch_backward_n<2>(a, s); break;
         case 4: st = launch_backward_n<4>(a, s); break;

@@ -172,3 +172,23 @@ def test_binary_q8_gradients_match_binary(gs, spp, n_hits):
         scale = np.abs(a[k]).max()
         assert scale > 0, k
         assert np.abs(a[k] - b[k]).max() <= 1e-5 * scale, k
+
+
+@pytest.mark.parametrize("spp,n_hits", [(16, 1), (5, 1), (8, 2), (64, 1)])
+def test_samples_per_lane_gradients_agree(gs, spp, n_hits):
+    """A lane carrying S consecutive samples (unused slots past the last
+    sample) re-traces the same per-sample hits: gradients equal one sample
+    per lane's up to the order of the float sums."""
+    cloud = scenes.shell_cloud(8, M=20000)
+    cam = scenes.default_camera(40, 30)
+    rng = np.random.default_rng(7)
+    d_rgb = rng.normal(size=(cam.width * cam.height, 3))
+    a = _gpu_grads(gs, cloud, cam, d_rgb, seed=3, spp=spp, n_hits=n_hits, samples_per_lane=1)
+    for S in (0, 2, 4):
+        if S * n_hits > 8:
+            continue
+        b = _gpu_grads(gs, cloud, cam, d_rgb, seed=3, spp=spp, n_hits=n_hits, samples_per_lane=S)
+        for k in KEYS:
+            scale = np.abs(a[k]).max()
+            assert scale > 0, k
+            assert np.abs(a[k] - b[k]).max() <= 1e-5 * scale, (S, k)
