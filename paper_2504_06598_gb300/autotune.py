@@ -1,6 +1,7 @@
 """Autotuner for the batched wavefront form.
 
-Picks the hierarchy node format (binary, 4-wide FP32, 4-wide 8-bit), the
+Picks the hierarchy node format (binary with FP32 or 8-bit wide copies,
+4-wide FP32, 4-wide 8-bit), the
 traversal stack capacity and the threads per block of gs_render_views by
 timing each combination on the caller's own workload (CUDA events on the
 launching stream, after a warm-up launch). The choice can be cached in a JSON
@@ -17,7 +18,7 @@ import torch
 
 from . import Bvh, Gaussians, build_bvh, render_views
 
-FORMATS = ("binary", "wide4", "wide4_q8")
+FORMATS = ("binary", "binary_q8", "wide4", "wide4_q8")
 STACKS = (48, 96)
 BLOCKS = (64, 128, 256)
 

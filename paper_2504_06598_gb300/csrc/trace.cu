@@ -223,14 +223,15 @@ gs_status launch_n(const TraceArgs &a, int format, bool count, cudaStream_t s) {
 // 1080p (trace ms, S = 1 against the choice): the time follows the number
 // of walks a pixel needs and grows slowly with the slots a walk carries,
 // so with T = spp * n_hits samples per pixel a lane takes K = n_hits * S
-// slots with K = T up to 2, K = 4 below T = 32 (spp 4: 14.1 -> 5.9 ms,
-// spp 8: 20.1 -> 9.6, spp 16: 24.2 -> 17.5, as per-lane packets of 1, 2
-// and 4 lanes per pixel), K = 2 from T = 32 (spp 64: 52.3 -> 31.6, one
-// walk of 32 lanes x 2 samples per pixel); never fewer than n_hits.
+// slots: K = T up to 2, K = 4 below T = 32 (spp 4: 14.1 -> 5.9 ms, spp 8:
+// 20.1 -> 9.6, spp 16: 24.2 -> 17.5, as per-lane packets of 1, 2 and 4
+// lanes per pixel), then K = T / 32 between 2 and 8, one walk of 32 lanes
+// per pixel (spp 64: 52.3 -> 31.6 ms; spp 128: 103.2 -> 37.0 with K = 4);
+// never fewer than n_hits.
 int auto_samples_per_lane(int spp, int n_hits, int node_format) {
     (void)node_format;
     const int64_t T = (int64_t)spp * n_hits;
-    int K = T <= 2 ? (int)T : (T < 32 ? 4 : 2);
+    int K = T <= 2 ? (int)T : (T < 32 ? 4 : (T >= 256 ? 8 : (T >= 128 ? 4 : 2)));
     if (K < n_hits) K = n_hits;
     return K / n_hits;
 }
