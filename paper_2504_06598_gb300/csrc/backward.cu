@@ -432,8 +432,8 @@ __global__ void __launch_bounds__(kThreads, LG >= 3 ? kGroupMinBlocks : 3) k_bac
             // nothing is in front of them and they never set the clip
 #pragma unroll
             for (int k = 0; k < N; ++k)
-                r.slot[k] = pass * N + k < a.n_samples ? Slot{INFINITY, INFINITY, 0.0f, 0xffffffffu}
-                                                       : Slot{-INFINITY, -INFINITY, 0.0f, 0xffffffffu};
+                r.slot[k] = pass * N + k < a.n_samples ? Slot{INFINITY, 0.0f, 0xffffffffu}
+                                                       : Slot{-INFINITY, 0.0f, 0xffffffffu};
             update_clip(r, a.t_max);
             if (!live) r.t_far = -INFINITY;
             if (a.n_nodes == 0) continue;
@@ -529,11 +529,18 @@ gs_status launch_backward_n(const TraceArgs &a, cudaStream_t s) {
 }  // namespace
 
 // Samples one lane of the gradient launch carries when the caller leaves
-// the choice to the library (samples_per_lane = 0).
+// the choice to the library (samples_per_lane = 0). Measured on the
+// 1M-Gaussian shell at 1080p (ms of gs_trace_backward, S = 1 against the
+// choice): with T = spp * n_hits samples per pixel a lane takes K =
+// n_hits * S slots, K = T up to 2, K = 4 below T = 16 (spp 4: 39.7 ->
+// 15.0, per-lane packets), else K = 2 (spp 16: 49.4 -> 46.0, spp 64:
+// 104.8 -> 59.8, 16- and 32-lane groups); never fewer than n_hits (N = 4
+// at spp 4 and 16 keeps S = 1: 48.1 and 77.8 ms against 50.1 and 103.8).
 static int auto_backward_samples_per_lane(int spp, int n_hits) {
-    (void)spp;
-    (void)n_hits;
-    return 1;
+    const int64_t T = (int64_t)spp * n_hits;
+    int K = T <= 2 ? (int)T : (T < 16 ? 4 : 2);
+    if (K < n_hits) K = n_hits;
+    return K / n_hits;
 }
 
 gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
@@ -565,6 +572,7 @@ gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinho
     a.tan_half = (float)tan((double)cam->fov_y_deg * 3.14159265358979323846 / 360.0);
     a.key0 = (uint32_t)(p->seed & 0xffffffffu);
     a.key1 = (uint32_t)(p->seed >> 32);
+    philox_round_keys(a.key0, a.key1, a.rk);
     a.stream_tag = p->stream_tag;
     a.spp = spp_eff;
     a.n_samples = p->spp * p->n_hits;

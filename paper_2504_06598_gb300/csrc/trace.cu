@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? group_min_blocks
             // at -inf: no candidate is closer, and it never sets the clip
 #pragma unroll
             for (int k = 0; k < N; ++k)
-                r.slot[k] = s0 + k < a.n_samples ? Slot{INFINITY, INFINITY, 0.0f, 0xffffffffu}
-                                                 : Slot{-INFINITY, -INFINITY, 0.0f, 0xffffffffu};
+                r.slot[k] = s0 + k < a.n_samples ? Slot{INFINITY, 0.0f, 0xffffffffu}
+                                                 : Slot{-INFINITY, 0.0f, 0xffffffffu};
             update_clip(r, a.t_max);
             if (!live) r.t_far = -INFINITY;  // lanes off the image never hit
             if (a.n_nodes > 0) {
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? group_min_blocks
                     if (a.hit_id) {
                         const int64_t o = ((int64_t)s0 + k) * npix + pix;
                         a.hit_id[o] = r.slot[k].gid == 0xffffffffu ? -1 : (int32_t)r.slot[k].gid;
-                        a.hit_t[o] = r.slot[k].t;
+                        a.hit_t[o] = r.slot[k].t();
                     }
                 }
             }
@@ -288,6 +288,7 @@ gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole 
     a.tan_half = (float)tan((double)cam->fov_y_deg * 3.14159265358979323846 / 360.0);
     a.key0 = (uint32_t)(p->seed & 0xffffffffu);
     a.key1 = (uint32_t)(p->seed >> 32);
+    philox_round_keys(a.key0, a.key1, a.rk);
     a.stream_tag = p->stream_tag;
     a.spp = spp_eff;
     a.n_samples = p->spp * p->n_hits;

@@ -33,6 +33,7 @@ struct TraceArgs {
     float eye[3], look_at[3], up[3];
     float tan_half;
     uint32_t key0, key1, stream_tag;
+    uint32_t rk[20];  // Philox round keys (key0, key1) + r * (0x9E3779B9, 0xBB67AE85)
     int spp;        // passes per pixel of the launch (each with N slots)
     int n_samples;  // samples per pixel; slots at s = pass * N + k >= n_samples are unused
     float t_min, t_max;
@@ -87,6 +88,28 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
     }
     return c;
+}
+
+// The same generator with its ten round keys precomputed on the host
+// (launch parameters), each round one 32x32->64-bit product per multiplier
+// and two three-input exclusive ors.
+__device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t rk[20]) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53ull;
+        const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57ull;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk[2 * r], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ rk[2 * r + 1], (uint32_t)p0);
+    }
+    return c;
+}
+
+// Round keys of philox10_rk for key (k0, k1).
+inline void philox_round_keys(uint32_t k0, uint32_t k1, uint32_t rk[20]) {
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
 }
 
 __device__ __forceinline__ float lane_to_unit(uint32_t u) {
@@ -216,10 +239,12 @@ __device__ __forceinline__ void sh_colour(const TraceArgs &a, uint32_t gid, cons
 
 // ---------------------------------------------------------------- slots
 struct Slot {
-    float t;    // tc + tau, rounded (used for range clipping and output)
     float tc;   // base-point parameter
     float tau;  // 1D mean relative to the base point
     uint32_t gid;
+    // the depth tc + tau, rounded once (range clipping and output); it is
+    // exactly the candidate depth the slot was filled from
+    __device__ __forceinline__ float t() const { return tc + tau; }
 };
 
 // (tc_a + tau_a, gid_a) < (tc_b + tau_b, gid_b), with the depth difference
@@ -255,14 +280,14 @@ __device__ __forceinline__ void set_ray(Ray<N> &r, const float o[3], const float
 template <int N>
 __device__ __forceinline__ void reset_slots(Ray<N> &r) {
 #pragma unroll
-    for (int k = 0; k < N; ++k) r.slot[k] = Slot{INFINITY, INFINITY, 0.0f, 0xffffffffu};
+    for (int k = 0; k < N; ++k) r.slot[k] = Slot{INFINITY, 0.0f, 0xffffffffu};
 }
 
 template <int N>
 __device__ __forceinline__ void update_clip(Ray<N> &r, float t_max) {
-    float far = r.slot[0].t;
+    float far = r.slot[0].t();
 #pragma unroll
-    for (int k = 1; k < N; ++k) far = fmaxf(far, r.slot[k].t);
+    for (int k = 1; k < N; ++k) far = fmaxf(far, r.slot[k].t());
     far = fminf(far, t_max);
     // expanded by 2^-19 relative so float32 slab rounding cannot cull a
     // node holding a hit that is (in exact arithmetic) not behind the clip
@@ -379,7 +404,6 @@ __device__ __forceinline__ void accept(const TraceArgs &a, Ray<N> &r, int pass, 
         for (int k = 0; k < N; ++k) {
             if (!closer[k]) continue;
             if (hash_xi(ph, s0 + k) < alpha) {
-                r.slot[k].t = t;
                 r.slot[k].tc = key_tc;
                 r.slot[k].tau = key_tau;
                 r.slot[k].gid = gid;
@@ -391,8 +415,8 @@ __device__ __forceinline__ void accept(const TraceArgs &a, Ray<N> &r, int pass, 
     }
     // one Philox call serves four consecutive samples
     uint4 u0 = make_uint4(0, 0, 0, 0), u1 = make_uint4(0, 0, 0, 0);
-    u0 = philox10(make_uint4(r.ray_id, gid, s0 >> 2, r.stream_tag), a.key0, a.key1);
-    if (N == 8) u1 = philox10(make_uint4(r.ray_id, gid, (s0 >> 2) + 1, r.stream_tag), a.key0, a.key1);
+    u0 = philox10_rk(make_uint4(r.ray_id, gid, s0 >> 2, r.stream_tag), a.rk);
+    if (N == 8) u1 = philox10_rk(make_uint4(r.ray_id, gid, (s0 >> 2) + 1, r.stream_tag), a.rk);
     if (COUNT) n_draws += 1 + (N == 8);
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -400,7 +424,6 @@ __device__ __forceinline__ void accept(const TraceArgs &a, Ray<N> &r, int pass, 
         const uint32_t s = s0 + k;
         const uint32_t bits = (N == 8 && k >= 4) ? pick(u1, s & 3) : pick(u0, s & 3);
         if (lane_to_unit(bits) < alpha) {
-            r.slot[k].t = t;
             r.slot[k].tc = key_tc;
             r.slot[k].tau = key_tau;
             r.slot[k].gid = gid;

@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks) k_render_view
             if (!live) r.t_far = -INFINITY;
             trace_pixel_ray<FMT, GLG, COUNT>(a, r, s, stack, stack_t, g_ref, g_t, err, cnt);
             n_cam += live;
-            const bool gauss = live && r.slot[0].gid != 0xffffffffu && r.slot[0].t < tq;
+            const bool gauss = live && r.slot[0].gid != 0xffffffffu && r.slot[0].t() < tq;
             const bool on_ground = live && ground && !gauss;
             float c[3] = {a.bg[0], a.bg[1], a.bg[2]};
             int32_t diag_cam = -1, diag_bounce = -1, diag_vis = 0;
@@ -612,6 +612,7 @@ gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_p
     for (int i = 0; i < 3; ++i) a.bg[i] = p->bg[i];
     a.key0 = (uint32_t)(p->seed & 0xffffffffu);
     a.key1 = (uint32_t)(p->seed >> 32);
+    philox_round_keys(a.key0, a.key1, a.rk);
     a.stream_tag = p->stream_tag;
     a.spp = p->spp;
     a.n_samples = p->spp;
