@@ -316,24 +316,33 @@ __device__ __forceinline__ float hash_xi(const float p[3], uint32_t s) {
 //   cand_alpha  the refined minimum q, the ellipsoid test q <= s^2 and alpha;
 //   accept      the draws of this lane's samples that are closer than their
 //               slots, replacing slots and clipping.
+// With RELOAD (the grouped traversal, whose leaf step is its register
+// peak) cand_alpha re-reads M and the opacity from the record, which L1
+// still holds, instead of keeping them live (measured 1-5% faster there;
+// the per-lane packets keep them, 2% faster so).
 struct CandGeom {
     float m[9];
     float w[3], md[3];
     float inv_dd, tau;
     float t, key_tc, key_tau;
     float opacity;
+    uint32_t idx;
     uint32_t gid;
 };
 
-template <int N>
+template <int N, bool RELOAD = false>
 __device__ __forceinline__ bool cand_depth(const TraceArgs &a, const Ray<N> &r, uint32_t idx,
                                            CandGeom &c) {
     const float4 *pp = reinterpret_cast<const float4 *>(a.prims + idx);
     const float4 p0 = __ldg(pp), p1 = __ldg(pp + 1), p2 = __ldg(pp + 2), p3 = __ldg(pp + 3);
     const float mu[3] = {p0.x, p0.y, p0.z};
-    c.m[0] = p1.x; c.m[1] = p1.y; c.m[2] = p1.z; c.m[3] = p1.w;
-    c.m[4] = p2.x; c.m[5] = p2.y; c.m[6] = p2.z; c.m[7] = p2.w; c.m[8] = p3.x;
-    c.opacity = p0.w;
+    const float m[9] = {p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w, p3.x};
+    if constexpr (!RELOAD) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) c.m[i] = m[i];
+        c.opacity = p0.w;
+    }
+    c.idx = idx;
     c.gid = __float_as_uint(p3.y);
     // o - mu = h + l exactly (two-sum)
     float h[3], l[3];
@@ -351,8 +360,8 @@ __device__ __forceinline__ bool cand_depth(const TraceArgs &a, const Ray<N> &r, 
     float mw[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        c.md[i] = fmaf(c.m[3 * i], r.d[0], fmaf(c.m[3 * i + 1], r.d[1], c.m[3 * i + 2] * r.d[2]));
-        mw[i] = fmaf(c.m[3 * i], c.w[0], fmaf(c.m[3 * i + 1], c.w[1], c.m[3 * i + 2] * c.w[2]));
+        c.md[i] = fmaf(m[3 * i], r.d[0], fmaf(m[3 * i + 1], r.d[1], m[3 * i + 2] * r.d[2]));
+        mw[i] = fmaf(m[3 * i], c.w[0], fmaf(m[3 * i + 1], c.w[1], m[3 * i + 2] * c.w[2]));
     }
     const float dd = fmaf(c.md[0], c.md[0], fmaf(c.md[1], c.md[1], c.md[2] * c.md[2]));
     const float wd = fmaf(mw[0], c.md[0], fmaf(mw[1], c.md[1], mw[2] * c.md[2]));
@@ -373,19 +382,32 @@ __device__ __forceinline__ bool cand_depth(const TraceArgs &a, const Ray<N> &r, 
 }
 
 // Refine the base point to the 1D mean, then the ellipsoid test (Eq. 2).
-template <int N>
-__device__ __forceinline__ bool cand_alpha(const Ray<N> &r, const CandGeom &c, float &alpha) {
+template <int N, bool RELOAD = false>
+__device__ __forceinline__ bool cand_alpha(const TraceArgs &a, const Ray<N> &r, const CandGeom &c,
+                                           float &alpha) {
+    float m[9], opacity;
+    if constexpr (RELOAD) {
+        const float4 *pp = reinterpret_cast<const float4 *>(a.prims + c.idx);
+        const float4 p0 = __ldg(pp), p1 = __ldg(pp + 1), p2 = __ldg(pp + 2), p3 = __ldg(pp + 3);
+        m[0] = p1.x; m[1] = p1.y; m[2] = p1.z; m[3] = p1.w;
+        m[4] = p2.x; m[5] = p2.y; m[6] = p2.z; m[7] = p2.w; m[8] = p3.x;
+        opacity = p0.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) m[i] = c.m[i];
+        opacity = c.opacity;
+    }
     float w2[3], mw2[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) w2[i] = fmaf(c.tau, r.d[i], c.w[i]);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-        mw2[i] = fmaf(c.m[3 * i], w2[0], fmaf(c.m[3 * i + 1], w2[1], c.m[3 * i + 2] * w2[2]));
+        mw2[i] = fmaf(m[3 * i], w2[0], fmaf(m[3 * i + 1], w2[1], m[3 * i + 2] * w2[2]));
     const float ww = fmaf(mw2[0], mw2[0], fmaf(mw2[1], mw2[1], mw2[2] * mw2[2]));
     const float wd2 = fmaf(mw2[0], c.md[0], fmaf(mw2[1], c.md[1], mw2[2] * c.md[2]));
     const float q = fmaxf(ww - wd2 * wd2 * c.inv_dd, 0.0f);
     if (!(q <= kS2)) return false;
-    alpha = c.opacity * expf(-0.5f * q);
+    alpha = opacity * expf(-0.5f * q);
     return true;
 }
 
@@ -460,7 +482,7 @@ __device__ __forceinline__ void intersect(const TraceArgs &a, Ray<N> &r, uint32_
     bool closer[N];
     if (!closer_slots<N>(r, c.t, c.key_tc, c.key_tau, c.gid, closer)) return;
     float alpha;
-    if (!cand_alpha<N>(r, c, alpha)) return;
+    if (!cand_alpha<N>(a, r, c, alpha)) return;
     accept<N, COUNT>(a, r, pass, closer, c.t, c.key_tc, c.key_tau, alpha, c.gid, n_draws);
 }
 
@@ -920,7 +942,7 @@ __device__ __forceinline__ void traverse_group(const TraceArgs &a, Ray<N> &r, in
             bool ok = false;
             if (hit && leaf) {
                 CandGeom c;
-                ok = cand_depth<N>(a, r, ref & ~kLeafBit, c) && cand_alpha<N>(r, c, cal);
+                ok = cand_depth<N, true>(a, r, ref & ~kLeafBit, c) && cand_alpha<N, true>(a, r, c, cal);
                 ct = c.t;
                 ck1 = c.key_tc;
                 ck2 = c.key_tau;
