@@ -31,11 +31,14 @@ namespace {
 // One candidate evaluated without acceptance, by the same formulas as
 // intersect(): base point, 1D mean, and the local coordinates of the point
 // on the ray at the mean.
+// M and the opacity are not kept: grad_alpha re-reads them from the record
+// (L1 still holds it), so fewer values stay live while the group sums the
+// candidate's weight.
 struct Cand {
-    float t, tc, tau, q, alpha, opacity;
+    float t, tc, tau, q, alpha;
     float v[3];  // x* - mu, world
     float u[3];  // M v = S^-1 R_q^T v
-    float m[9];
+    uint32_t idx;  // the Gaussian record
     uint32_t gid;
     bool valid;
 };
@@ -48,7 +51,7 @@ __device__ __forceinline__ Cand eval_cand(const TraceArgs &a, const float o[3], 
     const float mu[3] = {p0.x, p0.y, p0.z};
     const float m[9] = {p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w, p3.x};
     c.gid = __float_as_uint(p3.y);
-    c.opacity = p0.w;
+    c.idx = idx;
     float h[3], l[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -91,7 +94,6 @@ __device__ __forceinline__ Cand eval_cand(const TraceArgs &a, const float o[3], 
         c.v[i] = w2[i];
         c.u[i] = mw2[i];
     }
-    for (int i = 0; i < 9; ++i) c.m[i] = m[i];
     c.valid = (t > a.t_min) && (t < a.t_max) && (q <= kS2);
     return c;
 }
@@ -99,11 +101,15 @@ __device__ __forceinline__ Cand eval_cand(const TraceArgs &a, const float o[3], 
 // d alpha / d(mu, log s, quat, logit) of one candidate; alpha = o exp(-q/2),
 // q = |u|^2 with u = S^-1 R_q^T v, and t held at the 1D mean (dq/dt = 0).
 __device__ void grad_alpha(const TraceArgs &a, const Cand &c, float out[11]) {
+    const float4 *pp = reinterpret_cast<const float4 *>(a.prims + c.idx);
+    const float4 p0 = __ldg(pp), p1 = __ldg(pp + 1), p2 = __ldg(pp + 2), p3 = __ldg(pp + 3);
+    const float m[9] = {p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w, p3.x};
+    const float opacity = p0.w;
     const float dadq = -0.5f * c.alpha;
     // mean: dq/dmu = -2 M^T u
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-        out[j] = dadq * -2.0f * fmaf(c.m[j], c.u[0], fmaf(c.m[3 + j], c.u[1], c.m[6 + j] * c.u[2]));
+        out[j] = dadq * -2.0f * fmaf(m[j], c.u[0], fmaf(m[3 + j], c.u[1], m[6 + j] * c.u[2]));
     // log-scales: dq/dlog s_k = -2 u_k^2
     float inv_s[3];
 #pragma unroll
@@ -136,7 +142,7 @@ __device__ void grad_alpha(const TraceArgs &a, const Cand &c, float out[11]) {
     const float dot = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
 #pragma unroll
     for (int k = 0; k < 4; ++k) out[6 + k] = dadq * (gq[k] - dot * qh[k]) / n;
-    out[10] = c.alpha * (1.0f - c.opacity);
+    out[10] = c.alpha * (1.0f - opacity);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -376,9 +382,10 @@ __device__ void enumerate_group(const TraceArgs &a, const Ray<N> &r, const float
 
 // LG: log2 of the lanes per pixel when the grouped traversals are used, else
 // 0. The grouped form is latency-bound and built for eight resident blocks
-// per SM; the per-lane form for three.
+// per SM; the per-lane form for five (measured against three: 45.5 vs 48.5
+// ms at N=4 spp 4, 10.4 vs 13.1 ms at spp 2; four blocks equal to five).
 template <int N, int LG, bool Q8>
-__global__ void __launch_bounds__(kThreads, LG >= 3 ? kGroupMinBlocks : 3) k_backward(const TraceArgs a) {
+__global__ void __launch_bounds__(kThreads, LG >= 3 ? kGroupMinBlocks : 5) k_backward(const TraceArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;
     __shared__ uint32_t s_ref[LG >= 3 ? kThreads / 32 : 1][LG >= 3 ? kGroupPool : 1];
