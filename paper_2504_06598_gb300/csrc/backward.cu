@@ -31,18 +31,22 @@ namespace {
 // One candidate evaluated without acceptance, by the same formulas as
 // intersect(): base point, 1D mean, and the local coordinates of the point
 // on the ray at the mean.
-// M and the opacity are not kept: grad_alpha re-reads them from the record
-// (L1 still holds it), so fewer values stay live while the group sums the
-// candidate's weight.
+// With RELOAD (the grouped enumeration) M and the opacity are not kept:
+// grad_alpha re-reads them from the record (L1 still holds it), so fewer
+// values stay live while the group sums the candidate's weight (spp 16
+// 45.8 -> 43.4 ms, spp 64 60.7 -> 56.3); the per-lane form keeps them
+// (re-reading cost it 6-20%).
 struct Cand {
-    float t, tc, tau, q, alpha;
+    float t, tc, tau, q, alpha, opacity;
     float v[3];  // x* - mu, world
     float u[3];  // M v = S^-1 R_q^T v
+    float m[9];
     uint32_t idx;  // the Gaussian record
     uint32_t gid;
     bool valid;
 };
 
+template <bool RELOAD>
 __device__ __forceinline__ Cand eval_cand(const TraceArgs &a, const float o[3], const float d[3],
                                           uint32_t idx) {
     Cand c;
@@ -52,6 +56,11 @@ __device__ __forceinline__ Cand eval_cand(const TraceArgs &a, const float o[3], 
     const float m[9] = {p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w, p3.x};
     c.gid = __float_as_uint(p3.y);
     c.idx = idx;
+    if constexpr (!RELOAD) {
+        c.opacity = p0.w;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) c.m[i] = m[i];
+    }
     float h[3], l[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -100,11 +109,20 @@ __device__ __forceinline__ Cand eval_cand(const TraceArgs &a, const float o[3], 
 
 // d alpha / d(mu, log s, quat, logit) of one candidate; alpha = o exp(-q/2),
 // q = |u|^2 with u = S^-1 R_q^T v, and t held at the 1D mean (dq/dt = 0).
+template <bool RELOAD>
 __device__ void grad_alpha(const TraceArgs &a, const Cand &c, float out[11]) {
-    const float4 *pp = reinterpret_cast<const float4 *>(a.prims + c.idx);
-    const float4 p0 = __ldg(pp), p1 = __ldg(pp + 1), p2 = __ldg(pp + 2), p3 = __ldg(pp + 3);
-    const float m[9] = {p1.x, p1.y, p1.z, p1.w, p2.x, p2.y, p2.z, p2.w, p3.x};
-    const float opacity = p0.w;
+    float m[9], opacity;
+    if constexpr (RELOAD) {
+        const float4 *pp = reinterpret_cast<const float4 *>(a.prims + c.idx);
+        const float4 p0 = __ldg(pp), p1 = __ldg(pp + 1), p2 = __ldg(pp + 2), p3 = __ldg(pp + 3);
+        m[0] = p1.x; m[1] = p1.y; m[2] = p1.z; m[3] = p1.w;
+        m[4] = p2.x; m[5] = p2.y; m[6] = p2.z; m[7] = p2.w; m[8] = p3.x;
+        opacity = p0.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) m[i] = c.m[i];
+        opacity = c.opacity;
+    }
     const float dadq = -0.5f * c.alpha;
     // mean: dq/dmu = -2 M^T u
 #pragma unroll
@@ -165,7 +183,7 @@ __device__ __forceinline__ void leaf_gradient(const TraceArgs &a, const Ray<N> &
     uint32_t gid = 0;
     bool nz = false;
     if (hit) {
-        const Cand c = eval_cand(a, r.o, r.d, idx);
+        const Cand c = eval_cand<false>(a, r.o, r.d, idx);
         gid = c.gid;
         if (c.valid) {
             float coef = 0.0f;
@@ -184,7 +202,7 @@ __device__ __forceinline__ void leaf_gradient(const TraceArgs &a, const Ray<N> &
             if (any && coef != 0.0f) {
                 // a rejected hit has alpha <= xi < 1
                 coef /= (1.0f - c.alpha);
-                grad_alpha(a, c, contrib);
+                grad_alpha<false>(a, c, contrib);
 #pragma unroll
                 for (int j = 0; j < 11; ++j) contrib[j] *= coef;
                 nz = true;
@@ -309,7 +327,7 @@ __device__ void enumerate_group(const TraceArgs &a, const Ray<N> &r, const float
             float ci[3] = {0.0f, 0.0f, 0.0f};
             bool ok = false;
             if (hit && leaf) {
-                c = eval_cand(a, r.o, r.d, ref & ~kLeafBit);
+                c = eval_cand<true>(a, r.o, r.d, ref & ~kLeafBit);
                 // in front of some lane's winner only if t <= that lane's clip <= G
                 ok = c.valid && c.t <= G;
                 if (ok) sh_colour(a, c.gid, Y, ci);
@@ -339,7 +357,7 @@ __device__ void enumerate_group(const TraceArgs &a, const Ray<N> &r, const float
                 // a rejected hit has alpha <= xi < 1
                 const float w = my_coef / (1.0f - c.alpha);
                 float d[11];
-                grad_alpha(a, c, d);
+                grad_alpha<true>(a, c, d);
                 const int64_t gg = c.gid;
                 for (int k = 0; k < 3; ++k) {
                     atomicAdd(a.g_means + 3 * gg + k, d[k] * w);

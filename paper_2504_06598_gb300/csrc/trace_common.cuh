@@ -451,8 +451,15 @@ __device__ __forceinline__ void accept(const TraceArgs &a, Ray<N> &r, int pass, 
             r.slot[k].gid = gid;
         }
     }
+    if (r.any_hit) {
+        // a sample's visibility is known at its first accepted hit: that
+        // slot stops holding the clip and nothing is closer than it
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            if (r.slot[k].gid != 0xffffffffu) r.slot[k].tc = -INFINITY;
+    }
     update_clip(r, r.t_max);
-    if (r.any_hit && r.slot[0].gid != 0xffffffffu) r.t_far = -INFINITY;  // visibility known
+    if (r.any_hit && !(r.t_far > -INFINITY)) r.t_far = -INFINITY;  // every sample known
     // A projected-centre depth is not a ray parameter, so it cannot clip the
     // box tests: every box on the ray stays open and order is decided here.
     if (a.depth_mode == 1) r.t_far = r.t_max;

@@ -56,6 +56,7 @@ struct WaveArgs {
     int deferred;
     unsigned long long *codes;
     float *bounce_rgb;
+    int spl;  // samples per lane of the camera and shadow pass (1, 2 or 4)
 };
 
 // Sort code of a deferred bounce ray: 28 key bits (direction bin in an
@@ -119,14 +120,14 @@ __device__ __forceinline__ void bounce_dir(const TraceArgs &a, uint32_t ray_id, 
     for (int i = 0; i < 3; ++i) d[i] = __fdiv_rn(b[i], n);
 }
 
-template <int FMT, bool COUNT>
-__device__ __forceinline__ void trace_packet(const TraceArgs &a, Ray<1> &r, int pass,
+template <int FMT, bool COUNT, int K = 1>
+__device__ __forceinline__ void trace_packet(const TraceArgs &a, Ray<K> &r, int pass,
                                              uint32_t *stack, float *stack_t, uint32_t &err,
                                              Counts &cnt) {
     if (a.n_nodes == 0) return;
     if constexpr (FMT == GS_NODES_BINARY || FMT == GS_NODES_BINARY_Q8)
-        traverse_packet<1, COUNT>(a, r, pass, stack, stack_t, err, cnt);
-    else traverse_packet_wide<1, COUNT, FMT>(a, r, pass, stack, stack_t, err, cnt);
+        traverse_packet<K, COUNT>(a, r, pass, stack, stack_t, err, cnt);
+    else traverse_packet_wide<K, COUNT, FMT>(a, r, pass, stack, stack_t, err, cnt);
 }
 
 // Bounce rays leave each lane in its own direction: on binary nodes each
@@ -143,15 +144,27 @@ __device__ __forceinline__ void trace_own_ray(const TraceArgs &a, Ray<1> &r, int
 
 // Camera and shadow rays are one ray for all lanes of a pixel: with groups
 // of 2^GLG >= 8 lanes they take the grouped traversal of the wide copy.
-template <int FMT, int GLG, bool COUNT>
-__device__ __forceinline__ void trace_pixel_ray(const TraceArgs &a, Ray<1> &r, int pass,
+template <int FMT, int GLG, bool COUNT, int K = 1>
+__device__ __forceinline__ void trace_pixel_ray(const TraceArgs &a, Ray<K> &r, int pass,
                                                 uint32_t *stack, float *stack_t, uint32_t *g_ref,
                                                 float *g_t, uint32_t &err, Counts &cnt) {
     if (a.n_nodes == 0) return;
     if constexpr (GLG >= 3)
-        traverse_group<1, COUNT, GLG, false, FMT == GS_NODES_BINARY_Q8>(a, r, pass, g_ref, g_t, err,
+        traverse_group<K, COUNT, GLG, false, FMT == GS_NODES_BINARY_Q8>(a, r, pass, g_ref, g_t, err,
                                                                         cnt);
-    else trace_packet<FMT, COUNT>(a, r, pass, stack, stack_t, err, cnt);
+    else trace_packet<FMT, COUNT, K>(a, r, pass, stack, stack_t, err, cnt);
+}
+
+// Slots of pass `pass` of a lane carrying K samples: sample pass * K + k is
+// live below the pixel's sample count, the others sit at -inf (nothing is
+// closer, they never set the clip).
+template <int K>
+__device__ __forceinline__ void reset_live_slots(Ray<K> &r, int pass, int n_samples,
+                                                 const bool need[K]) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        r.slot[k] = need[k] && pass * K + k < n_samples ? Slot{INFINITY, 0.0f, 0xffffffffu}
+                                                        : Slot{-INFINITY, 0.0f, 0xffffffffu};
 }
 
 // Both passes of the batched form are latency-bound; they are built for 64
@@ -162,8 +175,11 @@ constexpr int kWaveMinBlocks = 4;
 
 // GLG: log2 of the lanes per pixel when the grouped traversal is used, else
 // 0. The group stacks are dynamic shared memory: per warp kGroupPool
-// references then kGroupPool entry distances.
-template <int FMT, int STACK, bool COUNT, int GLG>
+// references then kGroupPool entry distances. K: samples a lane carries
+// (slots of its camera and shadow rays); pass j of a lane holds samples
+// j * K .. j * K + K - 1 of its pixel, each with its own keys, outcome and
+// deferred bounce slot, exactly as K lanes with one sample each.
+template <int FMT, int STACK, bool COUNT, int GLG, int K = 1>
 __global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks) k_render_views(const WaveArgs w) {
     const TraceArgs &a = w.t;
     const int lane = threadIdx.x & 31;
@@ -180,6 +196,7 @@ __global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks) k_render_view
     const int lg = a.lpp_log2, L = 1 << lg;
     const int tw_lg = tile_w_log2(lg), th_lg = 5 - lg - tw_lg;
     const int sub = lane & (L - 1), pl = lane >> lg;
+    const int S = a.n_samples;  // samples per pixel
     uint32_t stack[STACK];
     float stack_t[STACK];
     uint32_t err = 0;
@@ -215,36 +232,43 @@ __global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks) k_render_view
             ground = tq > a.t_min && fabsf(p[0]) <= w.ground_half && fabsf(p[2]) <= w.ground_half;
             if (!ground) tq = INFINITY;
         }
-        // shadow directions and distances (fixed for the pixel)
         float acc[3] = {0.0f, 0.0f, 0.0f};
         const int n_rounds = (a.spp + L - 1) >> lg;
         for (int j = 0; j < n_rounds; ++j) {
-            const int s = (j << lg) + sub;
-            const bool live = valid && s < a.spp;
-            // camera ray
-            Ray<1> r;
+            const int pass = (j << lg) + sub;
+            bool live[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) live[k] = valid && pass * K + k < S;
+            // camera ray: K samples of the pixel's ray
+            Ray<K> r;
             set_ray(r, vw.eye, d0);
             r.ray_id = ray_id;
             r.stream_tag = a.stream_tag;
             r.t_min = a.t_min;
             r.t_max = a.t_max;
             r.any_hit = false;
-            reset_slots(r);
+            reset_live_slots<K>(r, pass, S, live);
             update_clip(r, r.t_max);
-            if (!live) r.t_far = -INFINITY;
-            trace_pixel_ray<FMT, GLG, COUNT>(a, r, s, stack, stack_t, g_ref, g_t, err, cnt);
-            n_cam += live;
-            const bool gauss = live && r.slot[0].gid != 0xffffffffu && r.slot[0].t() < tq;
-            const bool on_ground = live && ground && !gauss;
-            float c[3] = {a.bg[0], a.bg[1], a.bg[2]};
-            int32_t diag_cam = -1, diag_bounce = -1, diag_vis = 0;
-            if (gauss) {
-                sh_colour(a, r.slot[0].gid, Y0, c);
-                diag_cam = (int32_t)r.slot[0].gid;
-            }
-            if (on_ground) {
-                c[0] = c[1] = c[2] = 0.0f;
-                diag_cam = -2;
+            if (!live[0]) r.t_far = -INFINITY;
+            trace_pixel_ray<FMT, GLG, COUNT, K>(a, r, pass, stack, stack_t, g_ref, g_t, err, cnt);
+            float c[K][3];
+            bool on_ground[K];
+            int32_t diag_cam[K], diag_bounce[K], diag_vis[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                n_cam += live[k];
+                const bool gauss = live[k] && r.slot[k].gid != 0xffffffffu && r.slot[k].t() < tq;
+                on_ground[k] = live[k] && ground && !gauss;
+                c[k][0] = a.bg[0]; c[k][1] = a.bg[1]; c[k][2] = a.bg[2];
+                diag_cam[k] = -1; diag_bounce[k] = -1; diag_vis[k] = 0;
+                if (gauss) {
+                    sh_colour(a, r.slot[k].gid, Y0, c[k]);
+                    diag_cam[k] = (int32_t)r.slot[k].gid;
+                }
+                if (on_ground[k]) {
+                    c[k][0] = c[k][1] = c[k][2] = 0.0f;
+                    diag_cam[k] = -2;
+                }
             }
             // one shadow packet per light
             for (int l = 0; l < w.n_lights; ++l) {
@@ -255,38 +279,51 @@ __global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks) k_render_view
                 dist2 = __fadd_rn(dist2, __fmul_rn(wl[2], wl[2]));
                 const float dist = __fsqrt_rn(dist2);
                 for (int i = 0; i < 3; ++i) omega[i] = __fdiv_rn(wl[i], dist);
-                const bool need = on_ground && omega[1] > 0.0f && dist2 > 0.0f;
-                if (!__any_sync(kAll, need)) continue;
+                const bool lit = omega[1] > 0.0f && dist2 > 0.0f;
+                bool need[K];
+                bool any_need = false;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    need[k] = on_ground[k] && lit;
+                    any_need |= need[k];
+                }
+                if (!__any_sync(kAll, any_need)) continue;
                 // one ray for the pixel's lanes (the grouped traversal tests
-                // each child against the group's ray)
+                // each child against the group's ray), one slot per sample
                 const bool pix_ok = ground && dist2 > 0.0f;
-                Ray<1> sr;
+                Ray<K> sr;
                 set_ray(sr, p, pix_ok ? omega : d0);
                 sr.ray_id = ray_id;
                 sr.stream_tag = kTagShadow + (uint32_t)l;
                 sr.t_min = w.eps;
                 sr.t_max = dist;
                 sr.any_hit = true;
-                reset_slots(sr);
+                reset_live_slots<K>(sr, pass, S, need);
                 update_clip(sr, sr.t_max);
-                if (!need) sr.t_far = -INFINITY;
-                trace_pixel_ray<FMT, GLG, COUNT>(a, sr, s, stack, stack_t, g_ref, g_t, err, cnt);
-                n_shadow += need;
-                if (need && sr.slot[0].gid == 0xffffffffu) {
-                    diag_vis |= 1 << l;
-                    const float k = __fdiv_rn(omega[1], dist2);
-                    for (int i = 0; i < 3; ++i)
-                        c[i] = fmaf(w.albedo_over_pi[i] * w.light_int[l][i], k, c[i]);
+                if (!any_need) sr.t_far = -INFINITY;
+                trace_pixel_ray<FMT, GLG, COUNT, K>(a, sr, pass, stack, stack_t, g_ref, g_t, err, cnt);
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    n_shadow += need[k];
+                    if (need[k] && sr.slot[k].gid == 0xffffffffu) {
+                        diag_vis[k] |= 1 << l;
+                        const float kk = __fdiv_rn(omega[1], dist2);
+                        for (int i = 0; i < 3; ++i)
+                            c[k][i] = fmaf(w.albedo_over_pi[i] * w.light_int[l][i], kk, c[k][i]);
+                    }
                 }
             }
             // one diffuse bounce: deferred to the sorted bounce pass, or
-            // traced here
+            // traced here (one sample per lane only)
             if (w.bounce && w.deferred) {
-                if (live) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    if (!live[k]) continue;
+                    const int s = pass * K + k;
                     const int64_t gpix = vw.pix_begin + lpix;
-                    const int64_t slot = gpix * a.spp + s;
+                    const int64_t slot = gpix * S + s;
                     unsigned long long code = ~0ull;
-                    if (on_ground) {
+                    if (on_ground[k]) {
                         float db[3] = {0.0f, 1.0f, 0.0f};
                         bounce_dir(a, ray_id, (uint32_t)s, db);
                         code = bounce_code(w, p, db, gpix, s);
@@ -297,44 +334,49 @@ __global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks) k_render_view
                     w.bounce_rgb[3 * slot + 1] = 0.0f;
                     w.bounce_rgb[3 * slot + 2] = 0.0f;
                 }
-            } else if (w.bounce) {
-                float db[3] = {0.0f, 1.0f, 0.0f};
-                if (on_ground) bounce_dir(a, ray_id, (uint32_t)s, db);
-                const bool need = on_ground;
-                if (__any_sync(kAll, need)) {
-                    Ray<1> br;
-                    set_ray(br, p, db);
-                    br.ray_id = ray_id;
-                    br.stream_tag = kTagBounce;
-                    br.t_min = w.eps;
-                    br.t_max = INFINITY;
-                    br.any_hit = false;
-                    reset_slots(br);
-                    update_clip(br, br.t_max);
-                    if (!need) br.t_far = -INFINITY;
-                    trace_own_ray<FMT, COUNT>(a, br, s, stack, stack_t, err, cnt);
-                    n_bounce += need;
-                    if (need) {
-                        float lb[3] = {a.bg[0], a.bg[1], a.bg[2]};
-                        if (br.slot[0].gid != 0xffffffffu) {
-                            float Yb[16];
-                            sh_basis(a.sh_degree, db, Yb);
-                            sh_colour(a, br.slot[0].gid, Yb, lb);
-                            diag_bounce = (int32_t)br.slot[0].gid;
+            } else if constexpr (K == 1) {
+                if (w.bounce) {
+                    const int s = pass;
+                    float db[3] = {0.0f, 1.0f, 0.0f};
+                    if (on_ground[0]) bounce_dir(a, ray_id, (uint32_t)s, db);
+                    const bool need = on_ground[0];
+                    if (__any_sync(kAll, need)) {
+                        Ray<1> br;
+                        set_ray(br, p, db);
+                        br.ray_id = ray_id;
+                        br.stream_tag = kTagBounce;
+                        br.t_min = w.eps;
+                        br.t_max = INFINITY;
+                        br.any_hit = false;
+                        reset_slots(br);
+                        update_clip(br, br.t_max);
+                        if (!need) br.t_far = -INFINITY;
+                        trace_own_ray<FMT, COUNT>(a, br, s, stack, stack_t, err, cnt);
+                        n_bounce += need;
+                        if (need) {
+                            float lb[3] = {a.bg[0], a.bg[1], a.bg[2]};
+                            if (br.slot[0].gid != 0xffffffffu) {
+                                float Yb[16];
+                                sh_basis(a.sh_degree, db, Yb);
+                                sh_colour(a, br.slot[0].gid, Yb, lb);
+                                diag_bounce[0] = (int32_t)br.slot[0].gid;
+                            }
+                            for (int i = 0; i < 3; ++i) c[0][i] = fmaf(w.albedo[i], lb[i], c[0][i]);
                         }
-                        for (int i = 0; i < 3; ++i) c[i] = fmaf(w.albedo[i], lb[i], c[i]);
                     }
                 }
             }
-            if (live) {
-                acc[0] += c[0];
-                acc[1] += c[1];
-                acc[2] += c[2];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if (!live[k]) continue;
+                acc[0] += c[k][0];
+                acc[1] += c[k][1];
+                acc[2] += c[k][2];
                 if (w.samples) {
-                    const int64_t o = ((int64_t)s * w.n_pix + vw.pix_begin + lpix) * 3;
-                    w.samples[o] = diag_cam;
-                    w.samples[o + 1] = diag_bounce;
-                    w.samples[o + 2] = diag_vis;
+                    const int64_t o = ((int64_t)(pass * K + k) * w.n_pix + vw.pix_begin + lpix) * 3;
+                    w.samples[o] = diag_cam[k];
+                    w.samples[o + 1] = diag_bounce[k];
+                    w.samples[o + 2] = diag_vis[k];
                 }
             }
             __syncwarp();
@@ -346,7 +388,7 @@ __global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks) k_render_view
             acc[2] += __shfl_xor_sync(kAll, acc[2], o);
         }
         if (valid && sub == 0) {
-            const float inv_n = 1.0f / (float)a.spp;
+            const float inv_n = 1.0f / (float)S;
             const int64_t o = 3 * (vw.pix_begin + lpix);
             a.rgb[o] = acc[0] * inv_n;
             a.rgb[o + 1] = acc[1] * inv_n;
@@ -426,7 +468,7 @@ __global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks)
                 if (w.samples)
                     w.samples[((int64_t)s * w.n_pix + gpix) * 3 + 1] = (int32_t)br.slot[0].gid;
             }
-            const int64_t slot = gpix * a.spp + s;
+            const int64_t slot = gpix * a.n_samples + s;
             for (int c = 0; c < 3; ++c) w.bounce_rgb[3 * slot + c] = w.albedo[c] * lb[c];
         }
         __syncwarp();
@@ -441,10 +483,10 @@ __global__ void k_combine(const WaveArgs w) {
     if (px >= w.n_pix) return;
     const TraceArgs &a = w.t;
     float sum[3] = {0.0f, 0.0f, 0.0f};
-    const float *b = w.bounce_rgb + 3 * px * a.spp;
-    for (int s = 0; s < a.spp; ++s)
+    const float *b = w.bounce_rgb + 3 * px * a.n_samples;
+    for (int s = 0; s < a.n_samples; ++s)
         for (int c = 0; c < 3; ++c) sum[c] += b[3 * s + c];
-    const float inv_n = 1.0f / (float)a.spp;
+    const float inv_n = 1.0f / (float)a.n_samples;
     for (int c = 0; c < 3; ++c) a.rgb[3 * px + c] = fmaf(sum[c], inv_n, a.rgb[3 * px + c]);
 }
 
@@ -482,7 +524,7 @@ gs_status launch_bounce_f(const WaveArgs &w, const unsigned long long *codes, in
                  : launch_bounce<FMT, 96, false>(w, codes, n_slots, threads, s);
 }
 
-template <int FMT, int STACK, bool COUNT, int GLG>
+template <int FMT, int STACK, bool COUNT, int GLG, int K = 1>
 gs_status launch_views(const WaveArgs &w, int threads, cudaStream_t s) {
     int dev = 0, sms = 0, per = 0;
     const size_t smem = GLG >= 3 ? (size_t)(threads / 32) * 2 * kGroupPool * sizeof(uint32_t) : 0;
@@ -490,7 +532,7 @@ gs_status launch_views(const WaveArgs &w, int threads, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per, k_render_views<FMT, STACK, COUNT, GLG>, threads, smem);
+            &per, k_render_views<FMT, STACK, COUNT, GLG, K>, threads, smem);
     if (e != cudaSuccess) return cuda_fail(e, "render launch setup");
     const uint32_t warps_per_block = (uint32_t)threads / 32;
     uint32_t blocks = (uint32_t)sms * (uint32_t)(per > 0 ? per : 1);
@@ -499,13 +541,23 @@ gs_status launch_views(const WaveArgs &w, int threads, cudaStream_t s) {
     if (blocks == 0) return GS_OK;
     if ((e = cudaMemsetAsync(w.t.work, 0, sizeof(uint32_t), s)) != cudaSuccess)
         return cuda_fail(e, "reset work counter");
-    k_render_views<FMT, STACK, COUNT, GLG><<<blocks, threads, smem, s>>>(w);
+    k_render_views<FMT, STACK, COUNT, GLG, K><<<blocks, threads, smem, s>>>(w);
     return GS_OK;
 }
 
 template <int FMT, int GLG>
 gs_status launch_views_g(const WaveArgs &w, int threads, int stack, cudaStream_t s) {
     const bool count = w.counters != nullptr;
+    // several samples per lane: packets only (fewer than 8 lanes a pixel),
+    // never with counters
+    if constexpr (GLG == 0) {
+        if (!count && w.spl == 4)
+            return stack == 48 ? launch_views<FMT, 48, false, 0, 4>(w, threads, s)
+                               : launch_views<FMT, 96, false, 0, 4>(w, threads, s);
+        if (!count && w.spl == 2)
+            return stack == 48 ? launch_views<FMT, 48, false, 0, 2>(w, threads, s)
+                               : launch_views<FMT, 96, false, 0, 2>(w, threads, s);
+    }
     if (stack == 48)
         return count ? launch_views<FMT, 48, true, GLG>(w, threads, s)
                      : launch_views<FMT, 48, false, GLG>(w, threads, s);
@@ -614,7 +666,16 @@ gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_p
     a.key1 = (uint32_t)(p->seed >> 32);
     philox_round_keys(a.key0, a.key1, a.rk);
     a.stream_tag = p->stream_tag;
-    a.spp = p->spp;
+    // samples per lane of the camera and shadow pass: as the trace's choice
+    // below 32 samples per pixel (4, or 2 at spp 2-3), one otherwise, with
+    // counters, or with the bounce traced inline (measured on the 16-view
+    // benchmark frame at spp 16: see the design notes)
+    const int64_t bounce_slots = wave_slots(cams, n_views, ex, p);
+    const bool inline_bounce = ex && ex->bounce && ex->has_ground && bounce_slots == 0;
+    int K = 1;
+    if (counters == nullptr && !inline_bounce && p->spp >= 2 && p->spp < 32) K = p->spp >= 4 ? 4 : 2;
+    w.spl = K;
+    a.spp = (p->spp + K - 1) / K;
     a.n_samples = p->spp;
     a.t_min = p->t_min;
     a.t_max = p->t_max;
@@ -624,7 +685,7 @@ gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_p
     a.rgb = rgb;
     a.status = b->status;
     a.work = b->status + 1;
-    a.lpp_log2 = lanes_per_pixel_log2(p->spp);
+    a.lpp_log2 = lanes_per_pixel_log2(a.spp);
     if (b->node_depth && a.lpp_log2 >= 3) {
         a.grec = b->group[a.lpp_log2 - 3].rec;
         a.gcnt = b->group[a.lpp_log2 - 3].cnt;
@@ -675,7 +736,7 @@ gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_p
     const int threads = opt && opt->block_threads ? opt->block_threads : 128;
     // the bounce rays are sorted by direction and ground position and traced
     // in a pass of their own; the handle holds the scratch
-    const int64_t slots = wave_slots(cams, n_views, ex, p);
+    const int64_t slots = bounce_slots;
     gs_status st;
     if (slots > 0) {
         gs_bvh *mb = const_cast<gs_bvh *>(b);
