@@ -76,9 +76,10 @@ def run_wavefront(args):
     from the autotuner (searched on the same workload, one timed frame per
     candidate); each frame
     (hierarchy rebuild + the persistent render) is replayed from a CUDA graph.
-    The FP32 form and the reduced-precision form (FP16 SH, 8-bit boxes: the
-    8-bit wide copies or 8-bit 4-wide nodes, whichever the autotuner picks)
-    are timed side by side."""
+    The FP32 form, FP16 SH alone, and the reduced-precision form (FP16 SH
+    with 8-bit boxes in every traversal: at 16 spp the camera, shadow and
+    bounce rays run as per-lane packets, so the 8-bit 4-wide nodes) are
+    timed side by side."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -97,7 +98,8 @@ def run_wavefront(args):
            "forms": {}}
     base = None
     for name, dt, formats in (("fp32", torch.float32, ("binary", "wide4")),
-                              ("fp16-q8", torch.float16, ("binary_q8", "wide4_q8"))):
+                              ("fp16", torch.float16, ("binary", "wide4")),
+                              ("fp16-q8", torch.float16, ("wide4_q8",))):
         g = gs.Gaussians.from_cloud(cloud, sh_dtype=dt)
         tune = autotune.autotune(g, cams, ex, spp=spp, repeats=1, formats=formats)
         bvh = gs.build_bvh(g, node_format=tune["node_format"])

@@ -79,3 +79,18 @@ def test_hash_draw_statistics(gs):
     assert abs(z[0].mean()) < 0.15  # Philox: no bias
     assert np.mean(np.abs(z[1]) > 5) < 0.05  # hash: no gross outliers
     print("mean z: philox %.3f, hash %.3f" % (z[0].mean(), z[1].mean()))
+
+
+@pytest.mark.parametrize("mode", ["centre", "hash"])
+def test_variants_with_samples_per_lane(gs, mode):
+    """Both variants key their outcome on the sample index, so carrying
+    several samples per lane (grouped at spp 64, packets at spp 8) returns
+    the hits of one sample per lane."""
+    cloud = scenes.shell_cloud(2, M=20000)
+    cam = scenes.Pinhole(width=40, height=30, eye=(0.4, 0.3, 2.8), look_at=(0.1, 0.0, 0.0))
+    kw = dict(depth_mode=1) if mode == "centre" else dict(rng_mode=1)
+    for spp in (64, 8):
+        _, a = _run(gs, cloud, cam, seed=5, spp=spp, samples_per_lane=1, **kw)
+        for S in (2, 4, 0):
+            _, b = _run(gs, cloud, cam, seed=5, spp=spp, samples_per_lane=S, **kw)
+            assert np.array_equal(a, b), (spp, S)
