@@ -739,20 +739,30 @@ def main():
     ladder = {"n1_spp1": record(1, 1, args.steps), "n1_spp16": record(1, 16, args.steps)}
     bvh.sync_status()
 
-    # end to end through the public API: pinned host inputs, result read back
+    # end to end through the public API: pinned host inputs, result read back.
+    # The hierarchy needs the geometry only, so the SH coefficients (192 of
+    # the 236 MB) are copied on a second stream while the rebuild runs; the
+    # trace waits for them. Both copies are inside the timed region.
     host = {k: getattr(g, k).cpu().pin_memory() for k in
             ("means", "log_scales", "quats", "opacity_logits", "sh")}
     rgb_host = torch.empty((H_IMG, W_IMG, 3), dtype=torch.float32).pin_memory()
     h2d = sum(t.numel() * t.element_size() for t in host.values())
     d2h = rgb_host.numel() * 4
+    side = torch.cuda.Stream(device=dev)
     e2e_ms = []
     for k in range(args.warmup + args.steps):
         flush.fill_(float(k))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sh_done = torch.cuda.Event()
         e0.record(stream)
-        for name, t in host.items():
-            getattr(g, name).copy_(t, non_blocking=True)
+        side.wait_event(e0)
+        with torch.cuda.stream(side):
+            g.sh.copy_(host["sh"], non_blocking=True)
+            sh_done.record(side)
+        for name in ("means", "log_scales", "quats", "opacity_logits"):
+            getattr(g, name).copy_(host[name], non_blocking=True)
         bvh.rebuild(g)
+        stream.wait_event(sh_done)
         gs.trace_stochastic(bvh, g, cam, seed=0, spp=SPP_N1, n_hits=1, out=rgb)
         rgb_host.copy_(rgb, non_blocking=True)
         e1.record(stream)
