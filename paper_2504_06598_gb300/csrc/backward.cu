@@ -400,10 +400,13 @@ __device__ void enumerate_group(const TraceArgs &a, const Ray<N> &r, const float
 
 // LG: log2 of the lanes per pixel when the grouped traversals are used, else
 // 0. The grouped form is latency-bound and built for eight resident blocks
-// per SM; the per-lane form for five (measured against three: 45.5 vs 48.5
+// per SM with up to two slots per lane, seven with four or more (72
+// registers: N=4 spp 16 82.3 -> 79.0 ms; seven blocks cost 5-8% with two
+// slots); the per-lane form for five (measured against three: 45.5 vs 48.5
 // ms at N=4 spp 4, 10.4 vs 13.1 ms at spp 2; four blocks equal to five).
 template <int N, int LG, bool Q8>
-__global__ void __launch_bounds__(kThreads, LG >= 3 ? kGroupMinBlocks : 5) k_backward(const TraceArgs a) {
+__global__ void __launch_bounds__(kThreads, LG >= 3 ? (N >= 4 ? 7 : kGroupMinBlocks) : 5)
+    k_backward(const TraceArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;
     __shared__ uint32_t s_ref[LG >= 3 ? kThreads / 32 : 1][LG >= 3 ? kGroupPool : 1];

@@ -159,17 +159,19 @@ def test_background_and_ray_offset(gs, spp):
 
 
 def test_full_size_sampled_parity(gs):
-    """1M-Gaussian shell, the benchmark's 1080p view (N=1 and N=4, per-lane
-    packets at spp 1-2 and the grouped 8-wide traversal at spp 8-16),
-    checked on 768 sampled pixels, two thirds of them inside clusters."""
+    """1M-Gaussian shell, the benchmark's 1080p view, checked on 768 sampled
+    pixels, two thirds of them inside clusters: the four launches the
+    benchmark times (N=1 spp 64, N=4 spp 16, N=1 spp 1 and 16, each with the
+    library's choice of samples per lane) and one sample per lane at spp 2
+    (packets) and 8 (grouped 8-wide)."""
     cloud = scenes.shell_cloud(0)
     cam = scenes.default_camera(1920, 1080)
     g = gs.Gaussians.from_cloud(cloud)
     bvh = gs.build_bvh(g)
-    # (1, 64) and (4, 16) are the benchmark's own launches
-    for n_hits, spp in ((1, 2), (4, 1), (1, 8), (4, 16), (1, 64)):
+    for n_hits, spp, spl in ((1, 2, 1), (4, 1, 0), (1, 8, 1), (4, 16, 0), (1, 64, 0), (1, 1, 0),
+                             (1, 16, 0)):
         rgb, hid, _ = gs.trace_stochastic(bvh, g, cam, seed=0, spp=spp, n_hits=n_hits,
-                                          want_hits=True)
+                                          want_hits=True, samples_per_lane=spl)
         bvh.sync_status()
         S = spp * n_hits
         ids = hid.cpu().numpy().reshape(S, -1).T
