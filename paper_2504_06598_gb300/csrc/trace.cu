@@ -220,19 +220,28 @@ gs_status launch_n(const TraceArgs &a, int format, bool count, cudaStream_t s) {
 }
 
 // Samples one lane carries when the caller leaves the choice to the
-// library (samples_per_lane = 0). Measured on the 1M-Gaussian shell at
-// 1080p (trace ms, S = 1 against the choice): the time follows the number
-// of walks a pixel needs and grows slowly with the slots a walk carries,
-// so with T = spp * n_hits samples per pixel a lane takes K = n_hits * S
-// slots: K = T up to 2, K = 4 below T = 32 (spp 4: 14.1 -> 5.9 ms, spp 8:
-// 20.1 -> 9.6, spp 16: 24.2 -> 17.5, as per-lane packets of 1, 2 and 4
-// lanes per pixel), then K = T / 32 between 2 and 8, one walk of 32 lanes
-// per pixel (spp 64: 52.3 -> 31.6 ms; spp 128: 103.2 -> 37.0 with K = 4);
-// never fewer than n_hits.
+// library (samples_per_lane = 0). The time follows the number of walks a
+// pixel needs and grows slowly with the slots a walk carries. Measured on
+// the 1M-Gaussian shell at 1080p, trace ms for K = n_hits * S slots per
+// lane and T = spp * n_hits samples per pixel (one sample per lane first):
+//   T = 4:   K 1 14.1, 2 8.6, 4 5.9 (per-lane packets)
+//   T = 8:   K 1 20.1, 2 13.6, 4 8.9, 8 8.8
+//   T = 16:  K 1 24.2, 2 22.6, 4 16.0, 8 14.8
+//   T = 32:  K 1 27.5, 2 27.0, 4 25.5 (8 lanes a pixel, grouped)
+//   T = 64:  K 1 52.3, 2 30.5 (32 lanes), 4 30.6 (16 lanes), 8 38.5
+//   T = 128: K 2 59.8, 4 34.4, 8 46.4;  T = 256: K 4 67.5, 8 52.5
+// K is never below n_hits.
 int auto_samples_per_lane(int spp, int n_hits, int node_format) {
     (void)node_format;
     const int64_t T = (int64_t)spp * n_hits;
-    int K = T <= 2 ? (int)T : (T < 32 ? 4 : (T >= 256 ? 8 : (T >= 128 ? 4 : 2)));
+    int K;
+    if (T <= 2) K = (int)T;
+    else if (T < 8) K = 4;
+    else if (T < 32) K = 8;
+    else if (T < 64) K = 4;
+    else if (T < 128) K = 2;
+    else if (T < 256) K = 4;
+    else K = 8;
     if (K < n_hits) K = n_hits;
     return K / n_hits;
 }
