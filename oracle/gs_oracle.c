@@ -44,9 +44,8 @@
  *     later step promotes them to double.
  *
  * Pins: every function is checked by the -m "not gpu" tests against values
- * the paper prints, closed forms, brute force or library routines, except
- * the composition of the trigonometric hash draw (orc_hash_xi, Eq. 8-9):
- * its coefficients are pinned, its composition is parity unpinned.
+ * the paper prints, closed forms, invariants, brute force or library
+ * routines.
  */
 #include <math.h>
 #include <stdint.h>
@@ -138,9 +137,10 @@ double orc_xi(uint64_t seed, uint32_t ray_id, uint32_t gid, uint32_t sample, uin
  * rays; here the rays are fixed, so sample s hashes p + delta_s, with
  * delta_s = 1e-3 * (frac(s c1), frac(s c2), frac(s c3)) - 5e-4 from the
  * additive recurrence with c = (0.8191725134, 0.6710436067, 0.5497004779).
- * The coefficients are pinned to the paper's printed values; the
- * composition itself is parity unpinned: the paper prints no hash values,
- * so only its statistics (range, uniformity, near-unbiasedness) are tested. */
+ * The coefficients are pinned to the paper's printed values; the paper
+ * prints no hash values, so the composition is pinned through points where
+ * every sine is 0 or 1 (the draw is then a known fraction) and through the
+ * invariances the composition implies. */
 static const double kHashA1 = 91.3458;
 static const double kHashB1 = 47453.5453;
 static const double kHashA2[2] = {12.9898, 78.233};
