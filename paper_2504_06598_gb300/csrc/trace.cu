@@ -51,12 +51,14 @@ __host__ __device__ constexpr bool is_group_q8(int f) { return f >= kFmtGroupQ8 
 // resident blocks per SM with one or two slots per lane (64 registers),
 // seven with four (72: fewer spills of the four slots), five with eight;
 // the per-lane packet form for eight with up to four slots (against five:
-// spp 1 4.77 -> 4.31 ms, spp 16 with four slots 16.9 -> 15.9 ms).
+// spp 1 4.77 -> 4.31 ms, spp 16 with four slots 16.9 -> 15.9 ms) and six
+// with eight (85 registers; against one, four, five and eight blocks:
+// spp 16 with eight slots 14.8, 13.3, 12.4, 11.7 and 12.1 ms).
 constexpr int group_min_blocks(int n) { return n >= 8 ? 5 : (n >= 4 ? 7 : kGroupMinBlocks); }
 
 template <int N, bool COUNT, int FMT>
 __global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? group_min_blocks(N)
-                                                               : (N >= 8 ? 1 : 8))
+                                                               : (N >= 8 ? 6 : 8))
     k_trace(const TraceArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;

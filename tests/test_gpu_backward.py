@@ -47,7 +47,9 @@ def _gpu_grads(gs, cloud, cam, d_rgb, node_format="binary", **opts):
     return {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
 
 
-# spp >= 8 runs the grouped traversals (8, 16 and 32 lanes on one pixel)
+# the library's choice of samples per lane: per-lane packets at spp 2-4
+# (four slots), grouped traversals (8 or 16 lanes on one pixel, two slots)
+# at spp 16 and 40
 @pytest.mark.parametrize("spp,n_hits", [(4, 1), (2, 4), (3, 2), (40, 1), (16, 1), (8, 2)])
 def test_estimator_parity(gs, spp, n_hits):
     cloud = _cluster()
