@@ -226,11 +226,11 @@ gs_status launch_n(const TraceArgs &a, int format, bool count, cudaStream_t s) {
 // pixel needs and grows slowly with the slots a walk carries. Measured on
 // the 1M-Gaussian shell at 1080p, trace ms for K = n_hits * S slots per
 // lane and T = spp * n_hits samples per pixel (one sample per lane first):
-//   T = 4:   K 1 14.1, 2 8.6, 4 5.9 (per-lane packets)
-//   T = 8:   K 1 20.1, 2 13.6, 4 8.9, 8 8.8
-//   T = 16:  K 1 24.2, 2 22.6, 4 16.0, 8 14.8
-//   T = 32:  K 1 27.5, 2 27.0, 4 25.5 (8 lanes a pixel, grouped)
-//   T = 64:  K 1 52.3, 2 30.5 (32 lanes), 4 30.6 (16 lanes), 8 38.5
+//   T = 4:   K 1 14.1, 2 7.6, 4 5.4 (per-lane packets)
+//   T = 8:   K 1 20.1, 4 8.8, 8 7.1
+//   T = 16:  K 1 24.2, 4 15.9, 8 11.7
+//   T = 32:  K 1 27.5, 2 27.0, 4 25.5 (8 lanes a pixel, grouped), 8 21.0
+//   T = 64:  K 1 52.3, 2 30.4 (32 lanes, grouped), 4 30.5, 8 38.5
 //   T = 128: K 2 59.8, 4 34.4, 8 46.4;  T = 256: K 4 67.5, 8 52.5
 // K is never below n_hits.
 int auto_samples_per_lane(int spp, int n_hits, int node_format) {
@@ -239,8 +239,7 @@ int auto_samples_per_lane(int spp, int n_hits, int node_format) {
     int K;
     if (T <= 2) K = (int)T;
     else if (T < 8) K = 4;
-    else if (T < 32) K = 8;
-    else if (T < 64) K = 4;
+    else if (T < 64) K = 8;
     else if (T < 128) K = 2;
     else if (T < 256) K = 4;
     else K = 8;
