@@ -410,9 +410,14 @@ typedef struct gs_launch_options {
 
 /* Render n_views pinhole views (1..32, uneven sizes allowed). Warps take
  * pixel tiles from one queue over all views, the lanes of a pixel taking
- * its samples as in gs_trace_stochastic; camera and shadow rays are one ray
- * per pixel (grouped traversal of the wide copies on binary handles with
- * 8 or more lanes per pixel, warp packets otherwise). When the ground and
+ * its samples as in gs_trace_stochastic; below 64 samples per pixel (and
+ * without counters or an inline bounce) a lane carries several consecutive
+ * samples (8 from spp 8, 4 at spp 4-7, 2 at spp 2-3) as slots of one camera
+ * walk and of one
+ * shadow walk per light (a shadow slot ends at its first accepted
+ * Gaussian); per-sample outcomes do not depend on it. Camera and shadow
+ * rays are one ray per pixel (grouped traversal of the wide copies on
+ * binary handles with 8 or more lanes per pixel, warp packets otherwise). When the ground and
  * the bounce are on (and the views hold fewer than 2^24 - 1 pixels, spp <=
  * 1024) the bounce rays are deferred: each sample slot gets a sort code
  * (direction bin, then ground cell), the codes are radix-sorted, and a

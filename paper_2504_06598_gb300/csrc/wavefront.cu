@@ -180,7 +180,8 @@ constexpr int kWaveMinBlocks = 4;
 // j * K .. j * K + K - 1 of its pixel, each with its own keys, outcome and
 // deferred bounce slot, exactly as K lanes with one sample each.
 template <int FMT, int STACK, bool COUNT, int GLG, int K = 1>
-__global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks) k_render_views(const WaveArgs w) {
+__global__ void __launch_bounds__(kWaveMaxThreads, K >= 8 ? 3 : kWaveMinBlocks)
+    k_render_views(const WaveArgs w) {
     const TraceArgs &a = w.t;
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;
@@ -551,6 +552,9 @@ gs_status launch_views_g(const WaveArgs &w, int threads, int stack, cudaStream_t
     // several samples per lane: packets only (fewer than 8 lanes a pixel),
     // never with counters
     if constexpr (GLG == 0) {
+        if (!count && w.spl == 8)
+            return stack == 48 ? launch_views<FMT, 48, false, 0, 8>(w, threads, s)
+                               : launch_views<FMT, 96, false, 0, 8>(w, threads, s);
         if (!count && w.spl == 4)
             return stack == 48 ? launch_views<FMT, 48, false, 0, 4>(w, threads, s)
                                : launch_views<FMT, 96, false, 0, 4>(w, threads, s);
@@ -666,14 +670,18 @@ gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_p
     a.key1 = (uint32_t)(p->seed >> 32);
     philox_round_keys(a.key0, a.key1, a.rk);
     a.stream_tag = p->stream_tag;
-    // samples per lane of the camera and shadow pass: as the trace's choice
-    // below 32 samples per pixel (4, or 2 at spp 2-3), one otherwise, with
-    // counters, or with the bounce traced inline (measured on the 16-view
-    // benchmark frame at spp 16: see the design notes)
+    // samples per lane of the camera and shadow pass: 8 from spp 8 to 63
+    // (per-lane packets, the eight-slot kernel at three 256-thread blocks
+    // per SM), 4 at spp 4-7, 2 at spp 2-3; one from spp 64 (grouped), with
+    // counters, or with the bounce traced inline. Frame of 16 views 256^2
+    // to 1080p with ground, four lights and a bounce, one sample per lane
+    // -> four -> eight: spp 16 634 -> 472 -> 430 ms, spp 8 -> 269 -> 251,
+    // spp 32 806 (one) -> 770 (eight).
     const int64_t bounce_slots = wave_slots(cams, n_views, ex, p);
     const bool inline_bounce = ex && ex->bounce && ex->has_ground && bounce_slots == 0;
     int K = 1;
-    if (counters == nullptr && !inline_bounce && p->spp >= 2 && p->spp < 32) K = p->spp >= 4 ? 4 : 2;
+    if (counters == nullptr && !inline_bounce && p->spp >= 2 && p->spp < 64)
+        K = p->spp >= 8 ? 8 : (p->spp >= 4 ? 4 : 2);
     w.spl = K;
     a.spp = (p->spp + K - 1) / K;
     a.n_samples = p->spp;

@@ -99,9 +99,10 @@ def test_without_extras_matches_single_view_traces(gs, spp):
     packed = gs.render_views(bvh, g, cams, None, seed=3, spp=spp)
     views = gs.split_views(packed, cams)
     for cam, img in zip(cams, views):
-        # the batched form's lane layout (four samples per lane below 32
-        # samples per pixel), so the same summation order
-        ref = gs.trace_stochastic(bvh, g, cam, seed=3, spp=spp, samples_per_lane=4)
+        # the batched form's lane layout (eight samples per lane from spp 8,
+        # four at spp 4-7), so the same summation order
+        ref = gs.trace_stochastic(bvh, g, cam, seed=3, spp=spp,
+                                  samples_per_lane=8 if spp >= 8 else 4)
         assert torch.equal(img, ref)
     bvh.sync_status()
     bvh.free()
