@@ -145,6 +145,13 @@ def test_trace_layout_reports_the_mapping(gs):
     lay = gs.trace_layout(bvh, spp=3, n_hits=1, samples_per_lane=1)
     assert lay == {"samples_per_lane": 1, "lanes_per_pixel": 2, "passes": 3,
                    "grouped": False}
+    # the library's own choice: (samples per lane, lanes per pixel, grouped)
+    auto = {(1, 1): (1, 1, False), (4, 1): (4, 1, False), (16, 1): (8, 2, False),
+            (32, 1): (8, 4, False), (64, 1): (2, 32, True), (128, 1): (4, 32, True),
+            (256, 1): (8, 32, True), (16, 4): (1, 16, True), (4, 4): (2, 2, False)}
+    for (spp, n), want in auto.items():
+        lay = gs.trace_layout(bvh, spp=spp, n_hits=n)
+        assert (lay["samples_per_lane"], lay["lanes_per_pixel"], lay["grouped"]) == want, (spp, n)
     # S is capped at spp; invalid combinations are rejected
     assert gs.trace_layout(bvh, spp=2, n_hits=1, samples_per_lane=8)["samples_per_lane"] == 2
     with pytest.raises(gs.GsError):
