@@ -408,11 +408,20 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+def code_tokens(text):
+    """C/CUDA source with comments and blank space removed, so that a
+    comment edit does not count as a change of the kernel."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def trace_source_hash():
     h = hashlib.sha256()
     for name in ("trace.cu", "trace_common.cuh", "gsrt_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2504_06598_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2504_06598_gb300", "csrc", name)) as f:
+            h.update(code_tokens(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,12 +1,15 @@
 // trace.cu -- stochastic ray tracing of transparent Gaussians on sm_103a.
 //
-// One warp per tile of pixels, traversing as a packet (see traverse_packet).
-// With spp >= 2 the 32 lanes are split into pixels x samples: the L lanes of
-// one pixel trace passes sub, sub + L, ... of the same camera ray (L the
-// largest power of two not above spp, at most 32), so a packet shares its
-// ray and differs only in the random draws and the clip they cause; at
-// spp = 1 the tile is 8x4 pixels. Each pass is one traversal of the hierarchy
-// (Sec. 3.2) keeping N closest accepted intersections (Sec. 3.5). At every
+// One warp per tile of pixels. A lane carries S consecutive samples of its
+// pixel (the launch's passes have N * S slots, see launch_trace); the 32
+// lanes are split into pixels x lanes: the L lanes of one pixel trace passes
+// sub, sub + L, ... of the same camera ray (L the largest power of two not
+// above the passes, at most 32), so they share their ray and differ only in
+// the random draws and the clips they cause; with one pass per pixel the
+// tile is 8x4 pixels. With 8 or more lanes on a pixel the group walks the
+// L-wide copy together (traverse_group), otherwise the warp traverses as a
+// packet (traverse_packet). Each pass is one traversal of the hierarchy
+// (Sec. 3.2) keeping its closest accepted intersections (Sec. 3.5). At every
 // leaf the intersection routine of Alg. 1 runs:
 //   t    mean of the 1D Gaussian along the ray (Sec. 3.1)
 //   cull if t <= t_min or t is not before the slot's hit, or if the mean

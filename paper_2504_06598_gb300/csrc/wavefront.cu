@@ -3,15 +3,15 @@
 // among other assets cast soft shadows and light their surroundings).
 //
 // Warps take pixel tiles from one queue spanning every view (views of
-// uneven size balance through the queue). As in the single-view trace, the
-// L lanes of a pixel (L the largest power of two not above spp, at most 32)
-// take interleaved samples of it, so an 8x4 tile at spp = 1 becomes one
-// pixel x 32 samples at spp >= 32. For each round of samples a warp traces,
-// as packets: the camera rays of its lanes; for the lanes whose camera ray
-// reaches the ground first, one shadow packet per light (any-hit: a lane
-// stops at its first accepted Gaussian) and one bounce packet (closest
-// accepted Gaussian). Each ray type has its own Philox stream tag, so the
-// draws of the different rays of a sample are independent.
+// uneven size balance through the queue). As in the single-view trace a
+// lane carries K consecutive samples (slots) and the L lanes of a pixel
+// take interleaved passes of it. For each round a warp traces the camera
+// ray of its lanes (K slots each); for the samples whose camera ray reaches
+// the ground first, one shadow walk per light (any-hit: a slot stops at its
+// first accepted Gaussian); the bounce ray of each such sample is deferred
+// to a sorted pass of its own (or traced here, one sample per lane). Each
+// ray type has its own Philox stream tag, so the draws of the different
+// rays of a sample are independent.
 #include <cuda_runtime.h>
 #include <math.h>
 

@@ -89,6 +89,14 @@ def test_source_hash_covers_the_trace_sources():
     assert len(h) == 16 and int(h, 16) >= 0
 
 
+def test_code_tokens_ignore_comments_only():
+    a = "int f(int x) {  // the answer\n    return x + 1; /* one */ }\n"
+    b = "int f(int x) {\n  /* a different comment */ return x + 1;\n}"
+    c = "int f(int x) { return x + 2; }"
+    assert bench.code_tokens(a) == bench.code_tokens(b)
+    assert bench.code_tokens(a) != bench.code_tokens(c)
+
+
 def test_config_names_the_workload():
     cfg = bench.config_dict(None, 2)
     assert cfg["workload"] == "shell-1M-1080p"
