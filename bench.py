@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import itertools
 import json
 import os
 import subprocess
@@ -52,7 +53,8 @@ def parse():
                     help="skip the 3M-Gaussian precision-form record of the default run")
     ap.add_argument("--ref-pixels", type=int, default=512,
                     help="pixels per step of the reference (oracle) arm")
-    ap.add_argument("--case", choices=["trace-1080p", "wavefront-4v", "backward-1080p"], default=None,
+    ap.add_argument("--case", choices=["trace-1080p", "wavefront-4v", "backward-1080p",
+                                       "backward-retrace-1080p"], default=None,
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--n-hits", type=int, default=1, help="N of the profiling case")
     ap.add_argument("--case-spp", type=int, default=1, help="spp of the profiling case")
@@ -147,11 +149,15 @@ def run_wavefront(args):
 
 def run_backward(args):
     """Gradient form: the 1M shell and the 1080p view; one step = hierarchy
-    rebuild + the stochastic trace + gs_trace_backward of a seeded dLoss/dpixel
-    (gradient buffers zeroed inside the step), at N=1 spp=16 and N=4 spp=4.
-    Metric: gradient rays per second (pixels x spp / step time); each
-    gradient ray re-runs its forward traversal and enumerates the Gaussians
-    in front of its hit."""
+    rebuild + the stochastic trace + the gradient launch of a seeded
+    dLoss/dpixel (gradient buffers zeroed inside the step), at N=1 spp=16 and
+    N=4 spp=4. Metric: gradient rays per second (pixels x spp / step time).
+    Two forms each: the trace stores every sample's payload
+    (gs_trace_stochastic_keys) and the gradient launch reads it
+    (gs_trace_backward_keys), as the autograd path does; and "-retrace",
+    where the gradient launch runs each ray's forward traversal again
+    (gs_trace_backward). Either way it enumerates the Gaussians in front of
+    each hit."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -170,13 +176,16 @@ def run_backward(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     out = {"metric": "gradient form: Mrays/s of trace + backward at 1M Gaussians 1080p",
            "workload": "shell-1M-1080p-backward", "unit": "Mrays/s", "forms": {}}
-    for n_hits, spp in ((1, 16), (4, 4)):
+    for (n_hits, spp), stored in itertools.product(((1, 16), (4, 4)), (True, False)):
+        keys = gs.sample_keys(cam, spp, n_hits) if stored else None
+
         def step():
             for t in grads.values():
                 t.zero_()
             bvh.rebuild(g)
-            gs.trace_stochastic(bvh, g, cam, seed=0, spp=spp, n_hits=n_hits, out=rgb)
-            gs.trace_backward(bvh, g, cam, d_rgb, seed=0, spp=spp, n_hits=n_hits, grads=grads)
+            gs.trace_stochastic(bvh, g, cam, seed=0, spp=spp, n_hits=n_hits, out=rgb, keys=keys)
+            gs.trace_backward(bvh, g, cam, d_rgb, seed=0, spp=spp, n_hits=n_hits, grads=grads,
+                              keys=keys)
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
@@ -191,11 +200,13 @@ def run_backward(args):
             times.append(e0.elapsed_time(e1))
         bvh.sync_status()
         ms = float(np.mean(times))
-        out["forms"]["N%d-spp%d" % (n_hits, spp)] = {
+        out["forms"]["N%d-spp%d%s" % (n_hits, spp, "" if stored else "-retrace")] = {
             "ms_per_step": ms, "mrays_per_s": W_IMG * H_IMG * spp / (ms * 1e-3) / 1e6,
             "msamples_per_s": W_IMG * H_IMG * spp * n_hits / (ms * 1e-3) / 1e6,
             "grad_norm_means": float(grads["means"].norm()),
-            "grad_norm_sh": float(grads["sh"].norm())}
+            "grad_norm_sh": float(grads["sh"].norm()),
+            "stored_payload_bytes": 0 if keys is None else keys.numel() * 4}
+        del keys
     bvh.free()
     print(json.dumps(out), flush=True)
 
@@ -299,8 +310,10 @@ def run_precision(args):
 def run_case(args):
     """Profiling cases on the 1M-Gaussian shell, each launched twice (warm-up
     launch, then the launch to capture), spp from --case-spp (default 1):
-    trace-1080p (the 1920x1080 view), backward-1080p (trace + gradients of
-    that view), wavefront-4v (the batched form on four 480x270 views)."""
+    trace-1080p (the 1920x1080 view), backward-1080p (trace storing every
+    sample's payload + gradients of that view from them),
+    backward-retrace-1080p (trace + gradients tracing the winners again),
+    wavefront-4v (the batched form on four 480x270 views)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -313,13 +326,19 @@ def run_case(args):
     if args.case == "trace-1080p":
         for _ in range(2):
             gs.trace_stochastic(bvh, g, cam, seed=0, spp=args.case_spp, n_hits=args.n_hits)
-    elif args.case == "backward-1080p":
-        # the gradient launch of the spp given (trace first, as a user would)
+    elif args.case in ("backward-1080p", "backward-retrace-1080p"):
+        # the gradient launch of the spp given, reading the payloads the
+        # trace stored or (retrace) tracing the winners again; trace first,
+        # as a user would
         rng = np.random.default_rng(3)
         d_rgb = torch.from_numpy(rng.normal(size=(H_IMG, W_IMG, 3)).astype(np.float32)).cuda()
+        keys = (gs.sample_keys(cam, args.case_spp, args.n_hits)
+                if args.case == "backward-1080p" else None)
         for _ in range(2):
-            gs.trace_stochastic(bvh, g, cam, seed=0, spp=args.case_spp, n_hits=args.n_hits)
-            gs.trace_backward(bvh, g, cam, d_rgb, seed=0, spp=args.case_spp, n_hits=args.n_hits)
+            gs.trace_stochastic(bvh, g, cam, seed=0, spp=args.case_spp, n_hits=args.n_hits,
+                                keys=keys)
+            gs.trace_backward(bvh, g, cam, d_rgb, seed=0, spp=args.case_spp, n_hits=args.n_hits,
+                              keys=keys)
     else:
         # the batched form on four 480x270 views with ground, lights, bounce
         cams = scenes.wavefront_views(4, seed=0, fixed_res=(480, 270))

@@ -280,6 +280,32 @@ gs_status gs_trace_stochastic(const gs_bvh *bvh, const gs_gaussians *g, const gs
                               const gs_trace_params *p, float *rgb_out, int32_t *hit_id_out,
                               float *hit_t_out, void *stream);
 
+/* The payload of one sample after its traversal (Eq. 6): the depth key of
+ * its closest accepted hit, split as the base-point parameter tc and the 1D
+ * mean relative to the base point tau (the hit depth is tc + tau, rounded
+ * once), and that Gaussian's id; {+inf, 0, 0xffffffff} when the sample
+ * accepted nothing. 12 bytes, 4-byte aligned. */
+typedef struct gs_sample_key {
+    float tc;
+    float tau;
+    uint32_t gid;
+} gs_sample_key;
+
+/* gs_trace_stochastic that also stores every sample's payload, so that
+ * gs_trace_backward_keys can take the gradient without tracing again.
+ *   rgb_out   as in gs_trace_stochastic
+ *   keys_out  device gs_sample_key[height][width][spp * n_hits]: entry s of
+ *             a pixel is its sample s, the same sample index as the first
+ *             two dimensions of gs_trace_stochastic's hit_id_out (sample
+ *             pass i, slot h: s = i * n_hits + h); key.gid and
+ *             key.tc + key.tau are that sample's hit_id_out and hit_t_out
+ * Same rules, options and errors as gs_trace_stochastic; keys_out NULL,
+ * not a device pointer or not 4-byte aligned returns GS_ERR_INVALID_ARG.
+ * The image equals gs_trace_stochastic's for the same arguments. */
+gs_status gs_trace_stochastic_keys(const gs_bvh *bvh, const gs_gaussians *g,
+                                   const gs_pinhole *cam, const gs_trace_params *p, float *rgb_out,
+                                   gs_sample_key *keys_out, void *stream);
+
 /* How gs_trace_stochastic(bvh, ..., p, ...) maps samples to lanes (host
  * call, nothing is enqueued). layout_out (host int32[4]) receives
  * {samples per lane S, lanes per pixel L, passes ceil(spp / S) of
@@ -309,7 +335,8 @@ gs_status gs_probe_copy(const void *src, void *dst, int64_t bytes, int32_t repea
  * expectation is the gradient of the sorted blend of Eq. 3 (depth-order
  * swaps and the ellipsoid cutoff are not differentiated). Hits are
  * recomputed with the same keys as gs_trace_stochastic(bvh, g, cam, p), so
- * the samples are the ones that trace rendered; no per-ray list is stored.
+ * the samples are the ones that trace rendered; nothing is stored between
+ * the two calls (gs_trace_backward_keys takes the stored payloads instead).
  *   d_rgb            device float[height][width][3], dLoss/d(rgb_out)
  *   d_means          device float[M][3]     } gradients, ACCUMULATED (+=),
  *   d_log_scales     device float[M][3]     } float32 whatever sh_dtype is;
@@ -324,6 +351,24 @@ gs_status gs_trace_backward(const gs_bvh *bvh, const gs_gaussians *g, const gs_p
                             const gs_trace_params *p, const float *d_rgb, float *d_means,
                             float *d_log_scales, float *d_quats, float *d_opacity_logits,
                             float *d_sh, void *stream);
+
+/* gs_trace_backward with each sample's payload taken from `keys` instead
+ * of a second forward traversal (the rendering's traversal is skipped;
+ * the enumeration of the Gaussians in front of each winner remains).
+ *   keys  device gs_sample_key[height][width][spp * n_hits], written by
+ *         gs_trace_stochastic_keys with the same bvh, g, cam and p (seed,
+ *         spp, n_hits, t range, stream_tag); samples_per_lane may differ
+ * Other arguments, rules and errors as gs_trace_backward; keys NULL, not a
+ * device pointer or not 4-byte aligned returns GS_ERR_INVALID_ARG. Given
+ * the keys of that call, the gradients are those of gs_trace_backward (up
+ * to the atomics' summation order). A key whose gid is neither 0xffffffff
+ * nor below M is treated as no hit and makes gs_bvh_sync_status return
+ * GS_ERR_INVALID_ARG. */
+gs_status gs_trace_backward_keys(const gs_bvh *bvh, const gs_gaussians *g, const gs_pinhole *cam,
+                                 const gs_trace_params *p, const gs_sample_key *keys,
+                                 const float *d_rgb, float *d_means, float *d_log_scales,
+                                 float *d_quats, float *d_opacity_logits, float *d_sh,
+                                 void *stream);
 
 /* Allocation-free variant of gs_build_bvh. The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- for

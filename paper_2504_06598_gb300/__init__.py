@@ -89,9 +89,11 @@ _SIGNATURES = {
     "gs_bvh_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gs_trace_stochastic": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_trace_stochastic_keys": (C.c_int, [C.c_void_p] * 7),
     "gs_trace_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_trace_backward_keys": (C.c_int, [C.c_void_p] * 12),
     "gs_build_bvh_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p]),
     "gs_render_views": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
@@ -296,26 +298,64 @@ def build_bvh(g: Gaussians, stream=None, node_format="binary") -> Bvh:
 # ---------------------------------------------------------------- tracing
 
 
+def sample_keys(cam, spp=1, n_hits=1, device="cuda"):
+    """A buffer for every sample's payload (``gs_sample_key``: the depth key
+    tc, tau and the Gaussian id of its closest accepted hit), filled by
+    ``trace_stochastic(..., keys=)`` and read by ``trace_backward(...,
+    keys=)``: int32 [H, W, spp * n_hits, 3], the float fields as their bits.
+    12 bytes per sample."""
+    cam = cam if isinstance(cam, Camera) else Camera.of(cam)
+    return torch.empty((int(cam.height), int(cam.width), spp * n_hits, 3), dtype=torch.int32,
+                       device=device)
+
+
+def decode_keys(keys):
+    """(tc, tau, gid) of a ``sample_keys`` buffer: float32, float32, int64
+    (-1 where the sample accepted nothing)."""
+    tc = keys[..., 0].contiguous().view(torch.float32)
+    tau = keys[..., 1].contiguous().view(torch.float32)
+    return tc, tau, keys[..., 2].to(torch.int64)
+
+
+def _check_keys(keys, cam, spp, n_hits, dev):
+    H, W = int(cam.height), int(cam.width)
+    if (keys.dtype != torch.int32 or tuple(keys.shape) != (H, W, spp * n_hits, 3)
+            or not keys.is_contiguous() or keys.device != dev):
+        raise ValueError("keys must be a contiguous int32 tensor [%d, %d, %d, 3] on %s "
+                         "(sample_keys)" % (H, W, spp * n_hits, dev))
+
+
 def trace_stochastic(bvh: Bvh, g: Gaussians, cam, seed=0, spp=1, n_hits=1, t_min=0.0,
                      t_max=float("inf"), bg=(0.0, 0.0, 0.0), stack_depth=0, stream_tag=0,
                      want_hits=False, counters=None, out=None, stream=None, depth_mode=0,
-                     rng_mode=0, samples_per_lane=0):
+                     rng_mode=0, samples_per_lane=0, keys=None):
     """``gs_trace_stochastic``: render one pinhole view.
 
     Returns ``rgb`` [H, W, 3] float32 (and ``hit_id``, ``hit_t`` of shape
-    [spp, n_hits, H, W] when ``want_hits``), all on the current CUDA device."""
+    [spp, n_hits, H, W] when ``want_hits``), all on the current CUDA device.
+    With ``keys`` (a ``sample_keys`` buffer) the call is
+    ``gs_trace_stochastic_keys`` and also stores every sample's payload
+    there, for ``trace_backward(..., keys=keys)``."""
     cam = cam if isinstance(cam, Camera) else Camera.of(cam)
     H, W = int(cam.height), int(cam.width)
     dev = g.means.device
     rgb = out if out is not None else torch.empty((H, W, 3), dtype=torch.float32, device=dev)
-    hit_id = hit_t = None
-    if want_hits:
-        hit_id = torch.empty((spp, n_hits, H, W), dtype=torch.int32, device=dev)
-        hit_t = torch.empty((spp, n_hits, H, W), dtype=torch.float32, device=dev)
     gs = g.struct()
     cs = cam.struct()
     ps = _params(seed, spp, n_hits, t_min, t_max, bg, stack_depth, stream_tag, counters,
                  depth_mode, rng_mode, samples_per_lane)
+    if keys is not None:
+        if want_hits:
+            raise ValueError("keys and want_hits are separate calls")
+        _check_keys(keys, cam, spp, n_hits, dev)
+        _check(lib().gs_trace_stochastic_keys(
+            bvh.handle, C.byref(gs), C.byref(cs), C.byref(ps), C.c_void_p(rgb.data_ptr()),
+            C.c_void_p(keys.data_ptr()), _stream_handle(stream)))
+        return rgb
+    hit_id = hit_t = None
+    if want_hits:
+        hit_id = torch.empty((spp, n_hits, H, W), dtype=torch.int32, device=dev)
+        hit_t = torch.empty((spp, n_hits, H, W), dtype=torch.float32, device=dev)
     _check(lib().gs_trace_stochastic(
         bvh.handle, C.byref(gs), C.byref(cs), C.byref(ps), C.c_void_p(rgb.data_ptr()),
         None if hit_id is None else C.c_void_p(hit_id.data_ptr()),
@@ -347,11 +387,13 @@ def probe_copy(src, dst, repeats=1, stream=None):
 
 def trace_backward(bvh: Bvh, g: Gaussians, cam, d_rgb, seed=0, spp=1, n_hits=1, t_min=0.0,
                    t_max=float("inf"), bg=(0.0, 0.0, 0.0), stack_depth=0, stream_tag=0,
-                   grads=None, stream=None, samples_per_lane=0):
+                   grads=None, stream=None, samples_per_lane=0, keys=None):
     """``gs_trace_backward``: stochastic gradients of sum(d_rgb * rgb).
 
     Returns (and accumulates into, if given) a dict of float32 gradients
-    shaped like the parameters."""
+    shaped like the parameters. With ``keys`` (filled by
+    ``trace_stochastic(..., keys=)`` with the same options) the call is
+    ``gs_trace_backward_keys``: the winners are read instead of traced."""
     cam = cam if isinstance(cam, Camera) else Camera.of(cam)
     dev = g.means.device
     if grads is None:
@@ -364,11 +406,17 @@ def trace_backward(bvh: Bvh, g: Gaussians, cam, d_rgb, seed=0, spp=1, n_hits=1, 
     cs = cam.struct()
     ps = _params(seed, spp, n_hits, t_min, t_max, bg, stack_depth, stream_tag, None,
                  samples_per_lane=samples_per_lane)
-    _check(lib().gs_trace_backward(
-        bvh.handle, C.byref(gs_), C.byref(cs), C.byref(ps), C.c_void_p(d_rgb.data_ptr()),
-        C.c_void_p(grads["means"].data_ptr()), C.c_void_p(grads["log_scales"].data_ptr()),
-        C.c_void_p(grads["quats"].data_ptr()), C.c_void_p(grads["opacity_logits"].data_ptr()),
-        C.c_void_p(grads["sh"].data_ptr()), _stream_handle(stream)))
+    outs = [C.c_void_p(d_rgb.data_ptr()),
+            C.c_void_p(grads["means"].data_ptr()), C.c_void_p(grads["log_scales"].data_ptr()),
+            C.c_void_p(grads["quats"].data_ptr()), C.c_void_p(grads["opacity_logits"].data_ptr()),
+            C.c_void_p(grads["sh"].data_ptr()), _stream_handle(stream)]
+    if keys is not None:
+        _check_keys(keys, cam, spp, n_hits, dev)
+        _check(lib().gs_trace_backward_keys(bvh.handle, C.byref(gs_), C.byref(cs), C.byref(ps),
+                                            C.c_void_p(keys.data_ptr()), *outs))
+    else:
+        _check(lib().gs_trace_backward(bvh.handle, C.byref(gs_), C.byref(cs), C.byref(ps),
+                                       *outs))
     return grads
 
 
@@ -377,13 +425,17 @@ class StochasticRender(torch.autograd.Function):
 
     forward(means, log_scales, quats, opacity_logits, sh, sh_degree, cam,
     options) -> rgb [H, W, 3]; backward returns the unbiased stochastic
-    gradients of gs_trace_backward (same seed, same samples)."""
+    gradients of gs_trace_backward (same seed, same samples). With
+    ``keep_keys`` (the default) the forward stores every sample's payload
+    (12 bytes per sample) and the backward reads it instead of tracing
+    again (gs_trace_backward_keys)."""
 
     @staticmethod
     def forward(ctx, means, log_scales, quats, opacity_logits, sh, sh_degree, cam, options):
         options = dict(options)
         shared = options.pop("bvh", None)
         rebuild = options.pop("rebuild", True)
+        keep_keys = options.pop("keep_keys", True)
         g = Gaussians(means.detach(), log_scales.detach(), quats.detach(),
                       opacity_logits.detach(), sh.detach(), sh_degree)
         if shared is not None:
@@ -392,14 +444,18 @@ class StochasticRender(torch.autograd.Function):
             bvh = shared
         else:
             bvh = build_bvh(g)
-        rgb = trace_stochastic(bvh, g, cam, **options)
-        ctx.state = (bvh, shared is None, g, cam, options)
+        keys = None
+        if keep_keys:
+            keys = sample_keys(cam, options.get("spp", 1), options.get("n_hits", 1),
+                               device=means.device)
+        rgb = trace_stochastic(bvh, g, cam, keys=keys, **options)
+        ctx.state = (bvh, shared is None, g, cam, options, keys)
         return rgb
 
     @staticmethod
     def backward(ctx, d_rgb):
-        bvh, owned, g, cam, options = ctx.state
-        grads = trace_backward(bvh, g, cam, d_rgb, **options)
+        bvh, owned, g, cam, options, keys = ctx.state
+        grads = trace_backward(bvh, g, cam, d_rgb, keys=keys, **options)
         if owned:
             bvh.free()
         ctx.state = None
@@ -414,7 +470,9 @@ def render_differentiable(means, log_scales, quats, opacity_logits, sh, sh_degre
     a new one per call; its backward must run before the next forward that
     uses the same handle. ``rebuild=False`` uses that handle as it is: the
     caller has already rebuilt it from these same parameters (several views
-    of one parameter state share one rebuild)."""
+    of one parameter state share one rebuild). ``keep_keys=False`` stores
+    nothing between forward and backward: the backward traces the winners
+    again."""
     return StochasticRender.apply(means, log_scales, quats, opacity_logits, sh, sh_degree, cam,
                                   options)
 

@@ -282,6 +282,8 @@ gs_status gs_bvh_sync_status(gs_bvh *b, void *stream) {
     if (word & kErrNonfinite) return fail(GS_ERR_NONFINITE, "non-finite Gaussian parameter(s)");
     if (word & kErrStack) return fail(GS_ERR_STACK_OVERFLOW, "a ray overflowed its stack");
     if (word & kErrSteps) return fail(GS_ERR_STEP_LIMIT, "a ray exceeded the step limit");
+    if (word & kErrKeys)
+        return fail(GS_ERR_INVALID_ARG, "a stored sample key named no Gaussian of the handle");
     return GS_OK;
 }
 
@@ -353,6 +355,29 @@ static gs_status check_trace_args(const gs_bvh *b, const gs_gaussians *g, const 
     return GS_OK;
 }
 
+// The checks gs_trace_stochastic and gs_trace_stochastic_keys share.
+static gs_status check_trace_outputs(const gs_bvh *b, const gs_gaussians *g,
+                                     const gs_pinhole *cam, const gs_trace_params *p,
+                                     float *rgb_out) {
+    gs_status st = check_trace_args(b, g, cam, p);
+    if (st != GS_OK) return st;
+    if (!rgb_out) return fail(GS_ERR_INVALID_ARG, "rgb_out is NULL");
+    if ((st = check_device()) != GS_OK) return st;
+    if ((st = check_gaussians_device(g, true)) != GS_OK) return st;
+    if (!is_device_ptr(rgb_out)) return fail(GS_ERR_INVALID_ARG, "rgb_out is not a device pointer");
+    if (p->counters && !is_device_ptr(p->counters))
+        return fail(GS_ERR_INVALID_ARG, "counters is not a device pointer");
+    return GS_OK;
+}
+
+// A sample-key array argument: present, on the device, 4-byte aligned.
+static gs_status check_keys(const void *keys, const char *name) {
+    if (!keys) return fail(GS_ERR_INVALID_ARG, "%s is NULL", name);
+    if (((uintptr_t)keys & 3u) != 0) return fail(GS_ERR_INVALID_ARG, "%s is not 4-byte aligned", name);
+    if (!is_device_ptr(keys)) return fail(GS_ERR_INVALID_ARG, "%s is not a device pointer", name);
+    return GS_OK;
+}
+
 gs_status gs_trace_stochastic(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
                               const gs_trace_params *p, float *rgb_out, int32_t *hit_id_out,
                               float *hit_t_out, void *stream) {
@@ -361,14 +386,23 @@ gs_status gs_trace_stochastic(const gs_bvh *b, const gs_gaussians *g, const gs_p
     if (!rgb_out) return fail(GS_ERR_INVALID_ARG, "rgb_out is NULL");
     if ((hit_id_out == nullptr) != (hit_t_out == nullptr))
         return fail(GS_ERR_INVALID_ARG, "hit_id_out and hit_t_out go together");
-    if ((st = check_device()) != GS_OK) return st;
-    if ((st = check_gaussians_device(g, true)) != GS_OK) return st;
-    if (!is_device_ptr(rgb_out)) return fail(GS_ERR_INVALID_ARG, "rgb_out is not a device pointer");
+    if ((st = check_trace_outputs(b, g, cam, p, rgb_out)) != GS_OK) return st;
     if (hit_id_out && (!is_device_ptr(hit_id_out) || !is_device_ptr(hit_t_out)))
         return fail(GS_ERR_INVALID_ARG, "hit outputs must be device pointers");
-    if (p->counters && !is_device_ptr(p->counters))
-        return fail(GS_ERR_INVALID_ARG, "counters is not a device pointer");
-    return launch_trace(b, g, cam, p, rgb_out, hit_id_out, hit_t_out, (cudaStream_t)stream);
+    return launch_trace(b, g, cam, p, rgb_out, hit_id_out, hit_t_out, nullptr,
+                        (cudaStream_t)stream);
+}
+
+gs_status gs_trace_stochastic_keys(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
+                                   const gs_trace_params *p, float *rgb_out,
+                                   gs_sample_key *keys_out, void *stream) {
+    gs_status st = check_trace_args(b, g, cam, p);
+    if (st != GS_OK) return st;
+    if (!rgb_out) return fail(GS_ERR_INVALID_ARG, "rgb_out is NULL");
+    if (!keys_out) return fail(GS_ERR_INVALID_ARG, "keys_out is NULL");
+    if ((st = check_trace_outputs(b, g, cam, p, rgb_out)) != GS_OK) return st;
+    if ((st = check_keys(keys_out, "keys_out")) != GS_OK) return st;
+    return launch_trace(b, g, cam, p, rgb_out, nullptr, nullptr, keys_out, (cudaStream_t)stream);
 }
 
 gs_status gs_trace_layout(const gs_bvh *b, const gs_trace_params *p, int32_t *layout_out) {
@@ -389,10 +423,11 @@ gs_status gs_trace_layout(const gs_bvh *b, const gs_trace_params *p, int32_t *la
     return GS_OK;
 }
 
-gs_status gs_trace_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
-                            const gs_trace_params *p, const float *d_rgb, float *d_means,
-                            float *d_log_scales, float *d_quats, float *d_opacity_logits,
-                            float *d_sh, void *stream) {
+static gs_status backward_common(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
+                                 const gs_trace_params *p, const gs_sample_key *keys,
+                                 const float *d_rgb, float *d_means, float *d_log_scales,
+                                 float *d_quats, float *d_opacity_logits, float *d_sh,
+                                 void *stream) {
     gs_status st = check_trace_args(b, g, cam, p);
     if (st != GS_OK) return st;
     if (p->depth_mode != 0 || p->rng_mode != 0)
@@ -406,9 +441,30 @@ gs_status gs_trace_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pin
     const void *ptrs[6] = {d_rgb, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh};
     for (const void *q : ptrs)
         if (!is_device_ptr(q)) return fail(GS_ERR_INVALID_ARG, "gradient arrays must be device pointers");
+    if (keys && (st = check_keys(keys, "keys")) != GS_OK) return st;
     if (b->M == 0) return GS_OK;
-    return launch_backward(b, g, cam, p, d_rgb, d_means, d_log_scales, d_quats, d_opacity_logits,
-                           d_sh, (cudaStream_t)stream);
+    return launch_backward(b, g, cam, p, keys, d_rgb, d_means, d_log_scales, d_quats,
+                           d_opacity_logits, d_sh, (cudaStream_t)stream);
+}
+
+gs_status gs_trace_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
+                            const gs_trace_params *p, const float *d_rgb, float *d_means,
+                            float *d_log_scales, float *d_quats, float *d_opacity_logits,
+                            float *d_sh, void *stream) {
+    return backward_common(b, g, cam, p, nullptr, d_rgb, d_means, d_log_scales, d_quats,
+                           d_opacity_logits, d_sh, stream);
+}
+
+gs_status gs_trace_backward_keys(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
+                                 const gs_trace_params *p, const gs_sample_key *keys,
+                                 const float *d_rgb, float *d_means, float *d_log_scales,
+                                 float *d_quats, float *d_opacity_logits, float *d_sh,
+                                 void *stream) {
+    gs_status st = check_trace_args(b, g, cam, p);
+    if (st != GS_OK) return st;
+    if (!keys) return fail(GS_ERR_INVALID_ARG, "keys is NULL");
+    return backward_common(b, g, cam, p, keys, d_rgb, d_means, d_log_scales, d_quats,
+                           d_opacity_logits, d_sh, stream);
 }
 
 static gs_status check_camera(const gs_pinhole *cam) {

@@ -11,10 +11,11 @@
 // dL/dalpha_i = T_i (c_i - B_i) and dL/dc_i = T_i alpha_i. Order swaps and
 // the ellipsoid cutoff are not differentiated.
 //
-// Nothing is stored between the forward and backward passes: each pass
-// re-runs the forward traversal with the same keys (identical winners),
-// then a second traversal clipped at the winners' depths enumerates the
-// Gaussians in front of them. Gradients are accumulated with atomics: in
+// Each pass takes its samples' winners either from the payloads the
+// rendering stored (gs_trace_backward_keys) or by running the forward
+// traversal again with the same Philox keys (identical winners); then a
+// traversal clipped at the winners' depths enumerates the Gaussians in
+// front of them. Gradients are accumulated with atomics: in
 // the per-lane form reduced across the warp for the warp's shared leaf; in
 // the grouped form (8 or more lanes on one pixel, the wide copy of that
 // width) the chain rule runs once per Gaussian and group on the lanes'
@@ -475,11 +476,28 @@ __global__ void __launch_bounds__(kThreads, LG >= 3 ? (N >= 4 ? 7 : kGroupMinBlo
             update_clip(r, a.t_max);
             if (!live) r.t_far = -INFINITY;
             if (a.n_nodes == 0) continue;
-            // 1) the forward traversal: same keys, same winners
-            if constexpr (LG >= 3)
+            // 1) the winners: the rendering's stored payloads, or the forward
+            // traversal again with the same keys (same winners)
+            if (a.keys) {
+                if (live) {
+                    const gs_sample_key *kp = a.keys + pix * a.n_samples + pass * N;
+#pragma unroll
+                    for (int k = 0; k < N; ++k) {
+                        if (pass * N + k >= a.n_samples) continue;
+                        const float tc = __ldg(&kp[k].tc), tau = __ldg(&kp[k].tau);
+                        const uint32_t gid = __ldg(&kp[k].gid);
+                        if (gid == 0xffffffffu || gid < a.n_gauss) {
+                            r.slot[k] = Slot{tc, tau, gid};
+                        } else {
+                            err |= kErrKeys;  // names no Gaussian: no hit
+                        }
+                    }
+                }
+            } else if constexpr (LG >= 3) {
                 traverse_group<N, false, LG, false, Q8>(a, r, pass, grp_ref, grp_t, err, cnt);
-            else
+            } else {
                 traverse_packet<N, false>(a, r, pass, stack, stack_t, err, cnt);
+            }
             // the SH basis of the pixel's direction, formed per pass so that it
             // need not stay live between passes
             float Y[16];
@@ -586,9 +604,9 @@ static int auto_backward_samples_per_lane(int spp, int n_hits) {
 }
 
 gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
-                          const gs_trace_params *p, const float *d_rgb, float *d_means,
-                          float *d_log_scales, float *d_quats, float *d_logits, float *d_sh,
-                          cudaStream_t s) {
+                          const gs_trace_params *p, const gs_sample_key *keys, const float *d_rgb,
+                          float *d_means, float *d_log_scales, float *d_quats, float *d_logits,
+                          float *d_sh, cudaStream_t s) {
     // a lane carries S consecutive samples: ceil(spp / S) passes of
     // n_hits * S slots, the same sample indices and keys as the forward
     int S = p->samples_per_lane > 0 ? p->samples_per_lane
@@ -630,6 +648,8 @@ gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinho
         a.gcnt = b->group[a.lpp_log2 - 3].cnt;
         a.gq8 = b->node_format == GS_NODES_BINARY_Q8;
     }
+    a.keys = const_cast<gs_sample_key *>(keys);  // read only here
+    a.n_gauss = (uint32_t)b->M;
     a.d_rgb = d_rgb;
     a.log_scales = g->log_scales;
     a.quats = g->quats;

@@ -115,6 +115,7 @@ constexpr uint32_t kStepLimit = 1u << 22;  // node visits per ray and pass
 constexpr uint32_t kErrStack = 1u << 0;
 constexpr uint32_t kErrSteps = 1u << 1;
 constexpr uint32_t kErrNonfinite = 1u << 2;
+constexpr uint32_t kErrKeys = 1u << 3;  // a stored sample key named no Gaussian of the handle
 
 // s^2 of Eq. 2 with s = 2 sqrt(2).
 constexpr float kS2 = 8.0f;
@@ -191,10 +192,11 @@ int64_t wave_slots(const gs_pinhole *cams, int n_views, const gs_scene_extras *e
                    const gs_trace_params *p);
 
 // Backward (backward.cu)
+// keys: the rendering's per-sample payloads, or null to trace them again.
 gs_status launch_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
-                          const gs_trace_params *p, const float *d_rgb, float *d_means,
-                          float *d_log_scales, float *d_quats, float *d_logits, float *d_sh,
-                          cudaStream_t s);
+                          const gs_trace_params *p, const gs_sample_key *keys, const float *d_rgb,
+                          float *d_means, float *d_log_scales, float *d_quats, float *d_logits,
+                          float *d_sh, cudaStream_t s);
 
 // Wavefront (wavefront.cu)
 gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cams,
@@ -209,6 +211,6 @@ void trace_layout(const gs_bvh *b, const gs_trace_params *p, int *S, int *spp_ef
                   int *lpp_log2, bool *grouped);
 gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
                        const gs_trace_params *p, float *rgb, int32_t *hit_id, float *hit_t,
-                       cudaStream_t s);
+                       gs_sample_key *keys, cudaStream_t s);
 
 }  // namespace gsrt

@@ -151,6 +151,16 @@ __global__ void __launch_bounds__(kThreads, is_group_fmt(FMT) ? group_min_blocks
                         a.hit_t[o] = r.slot[k].t();
                     }
                 }
+                if (a.keys) {
+                    gs_sample_key *key = a.keys + pix * a.n_samples + s0;
+#pragma unroll
+                    for (int k = 0; k < N; ++k) {
+                        if (s0 + k >= a.n_samples) continue;
+                        key[k].tc = r.slot[k].tc;
+                        key[k].tau = r.slot[k].tau;
+                        key[k].gid = r.slot[k].gid;
+                    }
+                }
             }
             __syncwarp();
         }
@@ -268,7 +278,7 @@ void trace_layout(const gs_bvh *b, const gs_trace_params *p, int *S_out, int *sp
 
 gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
                        const gs_trace_params *p, float *rgb, int32_t *hit_id, float *hit_t,
-                       cudaStream_t s) {
+                       gs_sample_key *keys, cudaStream_t s) {
     int S = 1, spp_eff = 1, lpp_log2 = 0;
     bool grouped = false;
     trace_layout(b, p, &S, &spp_eff, &lpp_log2, &grouped);
@@ -314,6 +324,8 @@ gs_status launch_trace(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole 
     a.rgb = rgb;
     a.hit_id = hit_id;
     a.hit_t = hit_t;
+    a.keys = keys;
+    a.n_gauss = (uint32_t)b->M;
     a.counters = p->counters;
     a.status = b->status;
     a.work = b->status + 1;

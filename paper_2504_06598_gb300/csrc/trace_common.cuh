@@ -43,6 +43,10 @@ struct TraceArgs {
     float *rgb;
     int32_t *hit_id;
     float *hit_t;
+    // per-sample payloads [pixel][sample]: written by the trace when set;
+    // read by the backward when set, in place of its forward traversal
+    gs_sample_key *keys;
+    uint32_t n_gauss;  // Gaussians of the handle (bound on a stored key's id)
     unsigned long long *counters;
     uint32_t *status;
     uint32_t *work;  // tile counter of the persistent launch

@@ -60,6 +60,17 @@ def test_argument_errors_before_cuda(gs):
     assert L.gs_bvh_sync_status(None, None) == 1
     assert L.gs_bvh_free(None) == 0
     assert L.gs_trace_stochastic(None, None, None, None, None, None, None, None) == 1
+    assert L.gs_trace_stochastic_keys(None, None, None, None, None, None, None) == 1
+    assert L.gs_trace_backward_keys(*([None] * 12)) == 1
+
+
+def test_keys_struct_layout():
+    """gs_sample_key is {float tc, float tau, uint32 gid}: 12 bytes, and the
+    binding's int32 [..., 3] buffer has the same layout."""
+    text = open(os.path.join(ROOT, "include", "gsrt.h")).read()
+    body = re.search(r"typedef struct gs_sample_key \{(.*?)\} gs_sample_key;", text, re.S).group(1)
+    fields = re.findall(r"\b(float|uint32_t)\s+(\w+);", body)
+    assert fields == [("float", "tc"), ("float", "tau"), ("uint32_t", "gid")]
 
 
 def test_no_device_is_reported(gs):

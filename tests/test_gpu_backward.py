@@ -37,11 +37,20 @@ def _cluster(seed=0, M=60, sh_degree=1):
                                 sh_degree)
 
 
-def _gpu_grads(gs, cloud, cam, d_rgb, node_format="binary", **opts):
+def _gpu_grads(gs, cloud, cam, d_rgb, node_format="binary", keys=False, fwd_samples_per_lane=0,
+               **opts):
+    """Gradients of gs_trace_backward, or with keys=True of
+    gs_trace_backward_keys fed by a gs_trace_stochastic_keys rendering
+    (its own samples_per_lane, automatic by default)."""
     g = gs.Gaussians.from_cloud(cloud)
     bvh = gs.build_bvh(g, node_format=node_format)
     d = torch.from_numpy(np.ascontiguousarray(d_rgb, np.float32)).cuda().reshape(cam.height, cam.width, 3)
-    grads = gs.trace_backward(bvh, g, cam, d, **opts)
+    kb = None
+    if keys:
+        kb = gs.sample_keys(cam, opts.get("spp", 1), opts.get("n_hits", 1))
+        fwd = {k: v for k, v in opts.items() if k != "samples_per_lane"}
+        gs.trace_stochastic(bvh, g, cam, keys=kb, samples_per_lane=fwd_samples_per_lane, **fwd)
+    grads = gs.trace_backward(bvh, g, cam, d, keys=kb, **opts)
     bvh.sync_status()
     bvh.free()
     return {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
@@ -50,14 +59,17 @@ def _gpu_grads(gs, cloud, cam, d_rgb, node_format="binary", **opts):
 # the library's choice of samples per lane: per-lane packets at spp 2-4
 # (four slots), grouped traversals (8 or 16 lanes on one pixel, two slots)
 # at spp 16 and 40
+# keys: the winners read from the rendering's stored payloads instead of
+# traced again
+@pytest.mark.parametrize("keys", [False, True])
 @pytest.mark.parametrize("spp,n_hits", [(4, 1), (2, 4), (3, 2), (40, 1), (16, 1), (8, 2)])
-def test_estimator_parity(gs, spp, n_hits):
+def test_estimator_parity(gs, spp, n_hits, keys):
     cloud = _cluster()
     cam = scenes.Pinhole(width=16, height=12, fov_y_deg=9.0)
     rng = np.random.default_rng(spp)
     d_rgb = rng.normal(size=(cam.width * cam.height, 3))
     bg = (0.2, 0.1, 0.4)
-    gpu = _gpu_grads(gs, cloud, cam, d_rgb, seed=7, spp=spp, n_hits=n_hits, bg=bg)
+    gpu = _gpu_grads(gs, cloud, cam, d_rgb, keys=keys, seed=7, spp=spp, n_hits=n_hits, bg=bg)
     ref = oracle.grad_pinhole(cloud, cam, scenes.TraceSettings(seed=7, spp=spp, n_hits=n_hits, bg=bg),
                               d_rgb, mode="estimator")
     for k in KEYS:
@@ -194,3 +206,103 @@ def test_samples_per_lane_gradients_agree(gs, spp, n_hits):
             scale = np.abs(a[k]).max()
             assert scale > 0, k
             assert np.abs(a[k] - b[k]).max() <= 1e-5 * scale, (S, k)
+
+
+@pytest.mark.parametrize("spp,n_hits,S", [(1, 1, 0), (16, 1, 0), (16, 1, 1), (64, 1, 0),
+                                          (5, 1, 4), (4, 4, 0), (8, 2, 2), (2, 8, 0)])
+def test_keys_match_hits(gs, spp, n_hits, S):
+    """gs_trace_stochastic_keys renders the same image as gs_trace_stochastic
+    and stores each sample's payload: gid is the sample's hit id, tc + tau
+    (one float32 add) its hit depth, bit for bit."""
+    cloud = scenes.shell_cloud(8, M=20000)
+    cam = scenes.default_camera(45, 31)  # ragged against every tile shape
+    g = gs.Gaussians.from_cloud(cloud)
+    bvh = gs.build_bvh(g)
+    rgb, hid, ht = gs.trace_stochastic(bvh, g, cam, seed=4, spp=spp, n_hits=n_hits,
+                                       samples_per_lane=S, want_hits=True)
+    kb = gs.sample_keys(cam, spp, n_hits)
+    rgb2 = gs.trace_stochastic(bvh, g, cam, seed=4, spp=spp, n_hits=n_hits, samples_per_lane=S,
+                               keys=kb)
+    bvh.sync_status()
+    bvh.free()
+    assert torch.equal(rgb, rgb2)
+    tc, tau, gid = gs.decode_keys(kb)
+    # keys are [H, W, sample], hits [sample pass, slot, H, W]
+    hid = hid.reshape(spp * n_hits, cam.height, cam.width).permute(1, 2, 0).to(torch.int64)
+    ht = ht.reshape(spp * n_hits, cam.height, cam.width).permute(1, 2, 0)
+    assert torch.equal(gid, hid)
+    assert torch.equal((tc + tau)[gid >= 0], ht[gid >= 0])
+    assert bool(torch.isinf(tc[gid < 0]).all()) and bool((tau[gid < 0] == 0).all())
+    assert float((gid >= 0).float().mean()) > 0.05  # the view holds hits at all
+
+
+@pytest.mark.parametrize("spp,n_hits,fwd_S,bwd_S,fmt", [
+    (16, 1, 0, 0, "binary"), (16, 1, 1, 2, "binary"), (4, 4, 0, 0, "binary"),
+    (64, 1, 0, 0, "binary"), (7, 1, 8, 1, "binary"), (8, 2, 0, 4, "binary"),
+    (16, 1, 0, 0, "binary_q8"), (4, 1, 0, 0, "wide4_q8")])
+def test_keys_gradients_match_retrace(gs, spp, n_hits, fwd_S, bwd_S, fmt):
+    """Gradients from stored payloads equal those of tracing the winners
+    again, for any pair of rendering and gradient layouts, up to the order
+    of the atomic float sums."""
+    cloud = scenes.shell_cloud(8, M=20000)
+    cam = scenes.default_camera(40, 30)
+    rng = np.random.default_rng(11)
+    d_rgb = rng.normal(size=(cam.width * cam.height, 3))
+    a = _gpu_grads(gs, cloud, cam, d_rgb, node_format=fmt, seed=5, spp=spp, n_hits=n_hits,
+                   samples_per_lane=bwd_S)
+    b = _gpu_grads(gs, cloud, cam, d_rgb, node_format=fmt, keys=True, fwd_samples_per_lane=fwd_S,
+                   seed=5, spp=spp, n_hits=n_hits, samples_per_lane=bwd_S)
+    for k in KEYS:
+        scale = np.abs(a[k]).max()
+        assert scale > 0, k
+        assert np.abs(a[k] - b[k]).max() <= 1e-5 * scale, k
+
+
+def test_keys_with_unknown_gaussian_are_reported(gs):
+    """A key naming no Gaussian of the handle is checked before use: that
+    sample counts as no hit and gs_bvh_sync_status reports
+    GS_ERR_INVALID_ARG; the other samples' gradients are unchanged."""
+    cloud = scenes.shell_cloud(8, M=20000)
+    cam = scenes.default_camera(32, 24)
+    g = gs.Gaussians.from_cloud(cloud)
+    bvh = gs.build_bvh(g)
+    kb = gs.sample_keys(cam, 4, 1)
+    gs.trace_stochastic(bvh, g, cam, seed=1, spp=4, keys=kb)
+    d = torch.zeros((cam.height, cam.width, 3), device="cuda")
+    d[5:9, 7:12] = 1.0
+    ref = gs.trace_backward(bvh, g, cam, d, seed=1, spp=4, keys=kb)
+    bvh.sync_status()
+    bad = kb.clone()
+    bad[20, 3, 2, 2] = cloud.M + 5  # a pixel outside the weighted window
+    out = gs.trace_backward(bvh, g, cam, d, seed=1, spp=4, keys=bad)
+    with pytest.raises(gs.GsError) as e:
+        bvh.sync_status()
+    assert e.value.status == 1
+    bvh.sync_status()  # cleared
+    for k in KEYS:
+        scale = float(ref[k].abs().max())
+        assert float((ref[k] - out[k]).abs().max()) <= 1e-5 * scale, k
+    bvh.free()
+
+
+def test_keys_full_size(gs):
+    """1M-Gaussian shell at 1080p, N=1 spp 16 as the gradient benchmark
+    launches it (automatic layouts: eight samples per lane in the rendering,
+    two in the gradient launch): stored payloads and tracing the winners
+    again give the same gradients up to the atomics' summation order."""
+    cloud = scenes.shell_cloud(0, M=1_000_000)
+    cam = scenes.default_camera(1920, 1080)
+    g = gs.Gaussians.from_cloud(cloud)
+    bvh = gs.build_bvh(g)
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    d = torch.randn((1080, 1920, 3), device="cuda", generator=gen)
+    kb = gs.sample_keys(cam, 16, 1)
+    gs.trace_stochastic(bvh, g, cam, seed=0, spp=16, keys=kb)
+    a = gs.trace_backward(bvh, g, cam, d, seed=0, spp=16)
+    b = gs.trace_backward(bvh, g, cam, d, seed=0, spp=16, keys=kb)
+    bvh.sync_status()
+    bvh.free()
+    for k in KEYS:
+        scale = float(a[k].abs().max())
+        assert scale > 0, k
+        assert float((a[k] - b[k]).abs().max()) <= 1e-4 * scale, k
