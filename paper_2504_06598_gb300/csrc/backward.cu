@@ -417,7 +417,9 @@ __device__ void enumerate_group(const TraceArgs &a, const Ray<N> &r, const float
 // registers: N=4 spp 16 82.3 -> 79.0 ms; seven blocks cost 5-8% with two
 // slots); the per-lane form for five (measured against three: 45.5 vs 48.5
 // ms at N=4 spp 4, 10.4 vs 13.1 ms at spp 2; four blocks equal to five).
-template <int N, int LG, bool Q8>
+// KEYS: the winners come from the stored payloads (a.keys), and the
+// forward traversal is not compiled in.
+template <int N, int LG, bool Q8, bool KEYS>
 __global__ void __launch_bounds__(kThreads, LG >= 3 ? (N >= 4 ? 7 : kGroupMinBlocks) : 5)
     k_backward(const TraceArgs a) {
     const int lane = threadIdx.x & 31;
@@ -478,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, LG >= 3 ? (N >= 4 ? 7 : kGroupMinBlo
             if (a.n_nodes == 0) continue;
             // 1) the winners: the rendering's stored payloads, or the forward
             // traversal again with the same keys (same winners)
-            if (a.keys) {
+            if constexpr (KEYS) {
                 if (live) {
                     const gs_sample_key *kp = a.keys + pix * a.n_samples + pass * N;
 #pragma unroll
@@ -545,13 +547,14 @@ __global__ void __launch_bounds__(kThreads, LG >= 3 ? (N >= 4 ? 7 : kGroupMinBlo
     if (err) atomicOr(a.status, err);
 }
 
-template <int N, int LG, bool Q8>
+template <int N, int LG, bool Q8, bool KEYS>
 gs_status launch_backward_nl(const TraceArgs &a, cudaStream_t s) {
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_backward<N, LG, Q8>, kThreads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_backward<N, LG, Q8, KEYS>,
+                                                          kThreads, 0);
     if (e != cudaSuccess) return cuda_fail(e, "backward launch setup");
     const int tw_lg = tile_w_log2(a.lpp_log2), th_lg = 5 - a.lpp_log2 - tw_lg;
     const uint32_t tiles = (uint32_t)(((a.width + (1 << tw_lg) - 1) >> tw_lg) *
@@ -561,29 +564,34 @@ gs_status launch_backward_nl(const TraceArgs &a, cudaStream_t s) {
     if (blocks > max_blocks) blocks = max_blocks;
     if ((e = cudaMemsetAsync(a.work, 0, sizeof(uint32_t), s)) != cudaSuccess)
         return cuda_fail(e, "reset work counter");
-    k_backward<N, LG, Q8><<<blocks, kThreads, 0, s>>>(a);
+    k_backward<N, LG, Q8, KEYS><<<blocks, kThreads, 0, s>>>(a);
     return GS_OK;
 }
 
 // Groups of 8 or more lanes on one pixel use the wide copy of their width.
-template <int N>
-gs_status launch_backward_n(const TraceArgs &a, cudaStream_t s) {
+template <int N, bool KEYS>
+gs_status launch_backward_nk(const TraceArgs &a, cudaStream_t s) {
     if (a.grec != nullptr && a.gq8) {
         switch (a.lpp_log2) {
-            case 5: return launch_backward_nl<N, 5, true>(a, s);
-            case 4: return launch_backward_nl<N, 4, true>(a, s);
-            case 3: return launch_backward_nl<N, 3, true>(a, s);
+            case 5: return launch_backward_nl<N, 5, true, KEYS>(a, s);
+            case 4: return launch_backward_nl<N, 4, true, KEYS>(a, s);
+            case 3: return launch_backward_nl<N, 3, true, KEYS>(a, s);
             default: break;
         }
     } else if (a.grec != nullptr) {
         switch (a.lpp_log2) {
-            case 5: return launch_backward_nl<N, 5, false>(a, s);
-            case 4: return launch_backward_nl<N, 4, false>(a, s);
-            case 3: return launch_backward_nl<N, 3, false>(a, s);
+            case 5: return launch_backward_nl<N, 5, false, KEYS>(a, s);
+            case 4: return launch_backward_nl<N, 4, false, KEYS>(a, s);
+            case 3: return launch_backward_nl<N, 3, false, KEYS>(a, s);
             default: break;
         }
     }
-    return launch_backward_nl<N, 0, false>(a, s);
+    return launch_backward_nl<N, 0, false, KEYS>(a, s);
+}
+
+template <int N>
+gs_status launch_backward_n(const TraceArgs &a, cudaStream_t s) {
+    return a.keys ? launch_backward_nk<N, true>(a, s) : launch_backward_nk<N, false>(a, s);
 }
 
 }  // namespace
