@@ -418,9 +418,13 @@ __device__ void enumerate_group(const TraceArgs &a, const Ray<N> &r, const float
 // slots); the per-lane form for five (measured against three: 45.5 vs 48.5
 // ms at N=4 spp 4, 10.4 vs 13.1 ms at spp 2; four blocks equal to five).
 // KEYS: the winners come from the stored payloads (a.keys), and the
-// forward traversal is not compiled in.
+// forward traversal is not compiled in. Its per-lane form is built for six
+// blocks per SM (N=4 spp 4: 20.9 ms against 21.2 with five or four); its
+// grouped form keeps the re-tracing form's bounds (with two slots, seven
+// and six blocks: spp 16 19.9 and 21.6 ms against 19.5).
 template <int N, int LG, bool Q8, bool KEYS>
-__global__ void __launch_bounds__(kThreads, LG >= 3 ? (N >= 4 ? 7 : kGroupMinBlocks) : 5)
+__global__ void __launch_bounds__(kThreads, LG >= 3 ? (N >= 4 ? 7 : kGroupMinBlocks)
+                                                    : (KEYS ? 6 : 5))
     k_backward(const TraceArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t kAll = 0xffffffffu;
