@@ -466,9 +466,10 @@ typedef struct gs_launch_options {
  * the bounce are on (and the views hold fewer than 2^24 - 1 pixels, spp <=
  * 1024) the bounce rays are deferred: each sample slot gets a sort code
  * (direction bin, then ground cell), the codes are radix-sorted, and a
- * second pass traces the bounce rays as warp packets in that order and
+ * second pass traces the bounce rays in that order, 32 to a warp, each
+ * lane its own ray on binary nodes (a warp packet on 4-wide nodes), and
  * adds each pixel's bounce radiance in sample order; otherwise each lane
- * traces its bounce ray alone (binary nodes) or in a warp packet. The
+ * traces its bounce ray inline, the same way. The
  * deferred pass needs 28 bytes of device scratch per sample slot (total
  * pixels x spp), held by the handle and grown on first use (a synchronous
  * allocation; refused with GS_ERR_INVALID_ARG while `stream` is capturing

@@ -405,13 +405,16 @@ __global__ void __launch_bounds__(kWaveMaxThreads, K >= 8 ? 3 : kWaveMinBlocks)
     }
 }
 
-// Deferred bounce pass: warps take 32 consecutive sorted codes, so a packet
+// Deferred bounce pass: warps take 32 consecutive sorted codes, so a warp
 // holds bounce rays of nearby directions from nearby ground points (the
 // path tracer's wavefront regrouping of secondary rays). Each
 // lane rebuilds its sample's ground point and bounce direction with the
 // camera pass's arithmetic, traces, shades, and writes albedo x radiance to
-// the sample's slot. The first all-empty tile ends the pass (empty codes
-// sort last).
+// the sample's slot. On binary nodes each lane walks its own ray
+// (trace_own_ray): with the rays sorted, the lanes' walks stay close in
+// memory, and no lane visits nodes only its neighbours need (16-view frame
+// at spp 16: 430 -> 393 ms against a warp packet). The first all-empty
+// tile ends the pass (empty codes sort last).
 template <int FMT, int STACK, bool COUNT>
 __global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks)
     k_bounce(const WaveArgs w, const unsigned long long *__restrict__ codes, int64_t n_slots) {
@@ -459,7 +462,7 @@ __global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks)
         reset_slots(br);
         update_clip(br, br.t_max);
         if (!valid) br.t_far = -INFINITY;
-        trace_packet<FMT, COUNT>(a, br, s, stack, stack_t, err, cnt);
+        trace_own_ray<FMT, COUNT>(a, br, s, stack, stack_t, err, cnt);
         if (valid) {
             float lb[3] = {a.bg[0], a.bg[1], a.bg[2]};
             if (br.slot[0].gid != 0xffffffffu) {
