@@ -56,7 +56,7 @@ struct WaveArgs {
     int deferred;
     unsigned long long *codes;
     float *bounce_rgb;
-    int spl;  // samples per lane of the camera and shadow pass (1, 2 or 4)
+    int spl;  // samples per lane of the camera and shadow pass (1, 2, 4 or 8)
 };
 
 // Sort code of a deferred bounce ray: 28 key bits (direction bin in an
