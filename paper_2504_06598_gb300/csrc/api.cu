@@ -355,14 +355,12 @@ static gs_status check_trace_args(const gs_bvh *b, const gs_gaussians *g, const 
     return GS_OK;
 }
 
-// The checks gs_trace_stochastic and gs_trace_stochastic_keys share.
-static gs_status check_trace_outputs(const gs_bvh *b, const gs_gaussians *g,
-                                     const gs_pinhole *cam, const gs_trace_params *p,
+// The device-side checks gs_trace_stochastic and gs_trace_stochastic_keys
+// share (after check_trace_args and the NULL checks of their outputs).
+static gs_status check_trace_outputs(const gs_gaussians *g, const gs_trace_params *p,
                                      float *rgb_out) {
-    gs_status st = check_trace_args(b, g, cam, p);
+    gs_status st = check_device();
     if (st != GS_OK) return st;
-    if (!rgb_out) return fail(GS_ERR_INVALID_ARG, "rgb_out is NULL");
-    if ((st = check_device()) != GS_OK) return st;
     if ((st = check_gaussians_device(g, true)) != GS_OK) return st;
     if (!is_device_ptr(rgb_out)) return fail(GS_ERR_INVALID_ARG, "rgb_out is not a device pointer");
     if (p->counters && !is_device_ptr(p->counters))
@@ -386,7 +384,7 @@ gs_status gs_trace_stochastic(const gs_bvh *b, const gs_gaussians *g, const gs_p
     if (!rgb_out) return fail(GS_ERR_INVALID_ARG, "rgb_out is NULL");
     if ((hit_id_out == nullptr) != (hit_t_out == nullptr))
         return fail(GS_ERR_INVALID_ARG, "hit_id_out and hit_t_out go together");
-    if ((st = check_trace_outputs(b, g, cam, p, rgb_out)) != GS_OK) return st;
+    if ((st = check_trace_outputs(g, p, rgb_out)) != GS_OK) return st;
     if (hit_id_out && (!is_device_ptr(hit_id_out) || !is_device_ptr(hit_t_out)))
         return fail(GS_ERR_INVALID_ARG, "hit outputs must be device pointers");
     return launch_trace(b, g, cam, p, rgb_out, hit_id_out, hit_t_out, nullptr,
@@ -400,7 +398,7 @@ gs_status gs_trace_stochastic_keys(const gs_bvh *b, const gs_gaussians *g, const
     if (st != GS_OK) return st;
     if (!rgb_out) return fail(GS_ERR_INVALID_ARG, "rgb_out is NULL");
     if (!keys_out) return fail(GS_ERR_INVALID_ARG, "keys_out is NULL");
-    if ((st = check_trace_outputs(b, g, cam, p, rgb_out)) != GS_OK) return st;
+    if ((st = check_trace_outputs(g, p, rgb_out)) != GS_OK) return st;
     if ((st = check_keys(keys_out, "keys_out")) != GS_OK) return st;
     return launch_trace(b, g, cam, p, rgb_out, nullptr, nullptr, keys_out, (cudaStream_t)stream);
 }
@@ -423,13 +421,15 @@ gs_status gs_trace_layout(const gs_bvh *b, const gs_trace_params *p, int32_t *la
     return GS_OK;
 }
 
+// keyed: the caller is gs_trace_backward_keys, which requires keys.
 static gs_status backward_common(const gs_bvh *b, const gs_gaussians *g, const gs_pinhole *cam,
-                                 const gs_trace_params *p, const gs_sample_key *keys,
+                                 const gs_trace_params *p, bool keyed, const gs_sample_key *keys,
                                  const float *d_rgb, float *d_means, float *d_log_scales,
                                  float *d_quats, float *d_opacity_logits, float *d_sh,
                                  void *stream) {
     gs_status st = check_trace_args(b, g, cam, p);
     if (st != GS_OK) return st;
+    if (keyed && !keys) return fail(GS_ERR_INVALID_ARG, "keys is NULL");
     if (p->depth_mode != 0 || p->rng_mode != 0)
         return fail(GS_ERR_INVALID_ARG, "gradients need depth_mode 0 and rng_mode 0");
     if (!d_rgb || !d_means || !d_log_scales || !d_quats || !d_opacity_logits || !d_sh)
@@ -451,7 +451,7 @@ gs_status gs_trace_backward(const gs_bvh *b, const gs_gaussians *g, const gs_pin
                             const gs_trace_params *p, const float *d_rgb, float *d_means,
                             float *d_log_scales, float *d_quats, float *d_opacity_logits,
                             float *d_sh, void *stream) {
-    return backward_common(b, g, cam, p, nullptr, d_rgb, d_means, d_log_scales, d_quats,
+    return backward_common(b, g, cam, p, false, nullptr, d_rgb, d_means, d_log_scales, d_quats,
                            d_opacity_logits, d_sh, stream);
 }
 
@@ -460,10 +460,7 @@ gs_status gs_trace_backward_keys(const gs_bvh *b, const gs_gaussians *g, const g
                                  const float *d_rgb, float *d_means, float *d_log_scales,
                                  float *d_quats, float *d_opacity_logits, float *d_sh,
                                  void *stream) {
-    gs_status st = check_trace_args(b, g, cam, p);
-    if (st != GS_OK) return st;
-    if (!keys) return fail(GS_ERR_INVALID_ARG, "keys is NULL");
-    return backward_common(b, g, cam, p, keys, d_rgb, d_means, d_log_scales, d_quats,
+    return backward_common(b, g, cam, p, true, keys, d_rgb, d_means, d_log_scales, d_quats,
                            d_opacity_logits, d_sh, stream);
 }
 
