@@ -464,10 +464,11 @@ typedef struct gs_launch_options {
  * rays are one ray per pixel (grouped traversal of the wide copies on
  * binary handles with 8 or more lanes per pixel, warp packets otherwise). When the ground and
  * the bounce are on (and the views hold fewer than 2^24 - 1 pixels, spp <=
- * 1024) the bounce rays are deferred: each sample slot gets a sort code
- * (direction bin, then ground cell), the codes are radix-sorted, and a
- * second pass traces the bounce rays in that order, 32 to a warp, each
- * lane its own ray on binary nodes (a warp packet on 4-wide nodes), and
+ * 1024, pixels x spp <= 2^32 - 2^20) the bounce rays are deferred: each
+ * sample slot gets a sort code (direction bin, then ground cell), the codes
+ * are radix-sorted, and a second pass traces the bounce rays in that order,
+ * on binary nodes each lane its own ray, taking the next code as soon as
+ * its walk ends (a warp packet of 32 codes on 4-wide nodes), and
  * adds each pixel's bounce radiance in sample order; otherwise each lane
  * traces its bounce ray inline, the same way. The
  * deferred pass needs 28 bytes of device scratch per sample slot (total

@@ -405,16 +405,129 @@ __global__ void __launch_bounds__(kWaveMaxThreads, K >= 8 ? 3 : kWaveMinBlocks)
     }
 }
 
-// Deferred bounce pass: warps take 32 consecutive sorted codes, so a warp
-// holds bounce rays of nearby directions from nearby ground points (the
-// path tracer's wavefront regrouping of secondary rays). Each
-// lane rebuilds its sample's ground point and bounce direction with the
-// camera pass's arithmetic, traces, shades, and writes albedo x radiance to
-// the sample's slot. On binary nodes each lane walks its own ray
-// (trace_own_ray): with the rays sorted, the lanes' walks stay close in
-// memory, and no lane visits nodes only its neighbours need (16-view frame
-// at spp 16: 430 -> 393 ms against a warp packet). The first all-empty
-// tile ends the pass (empty codes sort last).
+// The bounce ray of a deferred sample code: the sample's ground point and
+// bounce direction rebuilt with the camera pass's arithmetic.
+__device__ __forceinline__ void bounce_ray(const WaveArgs &w, unsigned long long code, Ray<1> &br,
+                                           int64_t &gpix, int &s) {
+    gpix = (int64_t)((code >> 10) & 0xffffffull);
+    s = (int)(code & 1023ull);
+    int v = 0;
+    while (v + 1 < w.n_views && w.views[v + 1].pix_begin <= gpix) ++v;
+    const ViewDesc &vw = w.views[v];
+    const int64_t lpix = gpix - vw.pix_begin;
+    const int x = (int)(lpix % vw.width), y = (int)(lpix / vw.width);
+    const uint32_t ray_id = vw.ray_id_offset + (uint32_t)lpix;
+    float d0[3];
+    camera_ray_view(vw.eye, vw.look_at, vw.up, vw.tan_half, vw.width, vw.height, x, y, d0);
+    float p[3] = {0.0f, w.ground_y, 0.0f};
+    float db[3] = {0.0f, 1.0f, 0.0f};
+    const float tq = __fdiv_rn(__fsub_rn(w.ground_y, vw.eye[1]), d0[1]);
+    p[0] = __fadd_rn(vw.eye[0], __fmul_rn(tq, d0[0]));
+    p[2] = __fadd_rn(vw.eye[2], __fmul_rn(tq, d0[2]));
+    bounce_dir(w.t, ray_id, (uint32_t)s, db);
+    set_ray(br, p, db);
+    br.ray_id = ray_id;
+    br.stream_tag = kTagBounce;
+    br.t_min = w.eps;
+    br.t_max = INFINITY;
+    br.any_hit = false;
+    reset_slots(br);
+    update_clip(br, br.t_max);
+}
+
+// Shades a finished bounce ray and writes albedo x radiance to its slot.
+__device__ __forceinline__ void bounce_finish(const WaveArgs &w, const Ray<1> &br, int64_t gpix,
+                                              int s) {
+    const TraceArgs &a = w.t;
+    float lb[3] = {a.bg[0], a.bg[1], a.bg[2]};
+    if (br.slot[0].gid != 0xffffffffu) {
+        float Yb[16];
+        sh_basis(a.sh_degree, br.d, Yb);
+        sh_colour(a, br.slot[0].gid, Yb, lb);
+        if (w.samples) w.samples[((int64_t)s * w.n_pix + gpix) * 3 + 1] = (int32_t)br.slot[0].gid;
+    }
+    const int64_t slot = gpix * a.n_samples + s;
+    for (int c = 0; c < 3; ++c) w.bounce_rgb[3 * slot + c] = w.albedo[c] * lb[c];
+}
+
+// One step of traverse_lane's walk of the binary nodes, its state (node,
+// stack depth, steps) held by the caller: false once the walk has ended.
+template <bool COUNT>
+__device__ __forceinline__ bool lane_step(const TraceArgs &a, Ray<1> &r, int pass, uint32_t &node,
+                                          int &sp, uint32_t &steps, uint32_t *stack,
+                                          float *stack_t, uint32_t &err, Counts &cnt) {
+    if (++steps > a.step_limit) {
+        err |= kErrSteps;
+        return false;
+    }
+    if (COUNT) {
+        ++cnt.nodes;
+        ++cnt.node_fetch;
+    }
+    const float4 *np = reinterpret_cast<const float4 *>(a.nodes + node);
+    const float4 b0 = __ldg(np), b1 = __ldg(np + 1), b2 = __ldg(np + 2);
+    const uint4 cref = __ldg(reinterpret_cast<const uint4 *>(np + 3));
+    const float boxL[6] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
+    const float boxR[6] = {b1.z, b1.w, b2.x, b2.y, b2.z, b2.w};
+    float tL, tR;
+    bool hL = slab(boxL, r.inv, r.oinv, r.t_min, r.t_far, tL);
+    bool hR = slab(boxR, r.inv, r.oinv, r.t_min, r.t_far, tR);
+    const bool leafL = (cref.x & kLeafBit) != 0u, leafR = (cref.y & kLeafBit) != 0u;
+    if ((leafL && hL) || (leafR && hR)) {
+        const bool swap = leafL && leafR && hR && (!hL || tR < tL);
+        for (int li = 0; li < 2; ++li) {
+            const bool right = (li == 0) == swap;
+            if (!(right ? leafR : leafL) || !(right ? hR : hL)) continue;
+            if (COUNT) {
+                ++cnt.prims;
+                ++cnt.prim_fetch;
+            }
+            intersect<1, COUNT>(a, r, (right ? cref.y : cref.x) & ~kLeafBit, pass, cnt.draws);
+        }
+    }
+    hL = hL && !leafL && tL <= r.t_far;
+    hR = hR && !leafR && tR <= r.t_far;
+    if (hL && hR) {
+        if (sp >= a.stack_depth) {
+            err |= kErrStack;
+            return false;
+        }
+        const bool left_first = tL <= tR;
+        stack[sp] = left_first ? cref.y : cref.x;
+        stack_t[sp] = left_first ? tR : tL;
+        ++sp;
+        node = left_first ? cref.x : cref.y;
+        return true;
+    }
+    if (hL) {
+        node = cref.x;
+        return true;
+    }
+    if (hR) {
+        node = cref.y;
+        return true;
+    }
+    while (sp > 0) {
+        --sp;
+        if (stack_t[sp] <= r.t_far) {
+            node = stack[sp];
+            return true;
+        }
+    }
+    return false;
+}
+
+// Deferred bounce pass over the sorted codes (empty codes sort last), so
+// that a warp holds bounce rays of nearby directions from nearby ground
+// points (the path tracer's wavefront regrouping of secondary rays). On
+// binary nodes each lane walks its own ray, one node per loop step, and a
+// lane whose ray has ended takes the next code from the queue at once
+// (lanes that need one share an atomic): a warp's lanes stay busy instead
+// of waiting for its longest walk (the persistent traversal with ray
+// replacement of Aila and Laine, HPG 2009). Each lane shades its ray when
+// the walk ends and writes albedo x radiance to the sample's slot. On
+// 4-wide nodes a warp takes 32 consecutive codes and walks them as a
+// packet.
 template <int FMT, int STACK, bool COUNT>
 __global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks)
     k_bounce(const WaveArgs w, const unsigned long long *__restrict__ codes, int64_t n_slots) {
@@ -425,57 +538,73 @@ __global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks)
     float stack_t[STACK];
     uint32_t err = 0;
     Counts cnt;
-    for (;;) {
-        uint32_t tile = 0;
-        if (lane == 0) tile = atomicAdd(a.work, 1u);
-        tile = __shfl_sync(kAll, tile, 0);
-        if ((int64_t)tile * 32 >= n_slots) break;
-        const int64_t i = (int64_t)tile * 32 + lane;
-        const unsigned long long code = i < n_slots ? codes[i] : ~0ull;
-        const bool valid = code != ~0ull;
-        if (!__any_sync(kAll, valid)) break;
-        const int64_t gpix = valid ? (int64_t)((code >> 10) & 0xffffffull) : 0;
-        const int s = valid ? (int)(code & 1023ull) : 0;
-        int v = 0;
-        while (v + 1 < w.n_views && w.views[v + 1].pix_begin <= gpix) ++v;
-        const ViewDesc &vw = w.views[v];
-        const int64_t lpix = gpix - vw.pix_begin;
-        const int x = (int)(lpix % vw.width), y = (int)(lpix / vw.width);
-        const uint32_t ray_id = vw.ray_id_offset + (uint32_t)lpix;
-        float d0[3];
-        camera_ray_view(vw.eye, vw.look_at, vw.up, vw.tan_half, vw.width, vw.height, x, y, d0);
-        float p[3] = {0.0f, w.ground_y, 0.0f};
-        float db[3] = {0.0f, 1.0f, 0.0f};
-        if (valid) {
-            const float tq = __fdiv_rn(__fsub_rn(w.ground_y, vw.eye[1]), d0[1]);
-            p[0] = __fadd_rn(vw.eye[0], __fmul_rn(tq, d0[0]));
-            p[2] = __fadd_rn(vw.eye[2], __fmul_rn(tq, d0[2]));
-            bounce_dir(a, ray_id, (uint32_t)s, db);
-        }
+    if constexpr (FMT == GS_NODES_BINARY || FMT == GS_NODES_BINARY_Q8) {
+        // the work counter counts codes; the launcher keeps n_slots + the
+        // launch's threads below 2^32
+        bool active = false, more = true;
+        int64_t gpix = 0;
+        int s = 0;
         Ray<1> br;
-        set_ray(br, p, db);
-        br.ray_id = ray_id;
-        br.stream_tag = kTagBounce;
-        br.t_min = w.eps;
-        br.t_max = INFINITY;
-        br.any_hit = false;
-        reset_slots(br);
-        update_clip(br, br.t_max);
-        if (!valid) br.t_far = -INFINITY;
-        trace_own_ray<FMT, COUNT>(a, br, s, stack, stack_t, err, cnt);
-        if (valid) {
-            float lb[3] = {a.bg[0], a.bg[1], a.bg[2]};
-            if (br.slot[0].gid != 0xffffffffu) {
-                float Yb[16];
-                sh_basis(a.sh_degree, db, Yb);
-                sh_colour(a, br.slot[0].gid, Yb, lb);
-                if (w.samples)
-                    w.samples[((int64_t)s * w.n_pix + gpix) * 3 + 1] = (int32_t)br.slot[0].gid;
+        uint32_t node = 0, steps = 0;
+        int sp = 0;
+        for (;;) {
+            const uint32_t idle = __ballot_sync(kAll, !active && more);
+            if (idle) {
+                const int leader = __ffs(idle) - 1;
+                uint32_t first = 0;
+                if (lane == leader) first = atomicAdd(a.work, (uint32_t)__popc(idle));
+                first = __shfl_sync(kAll, first, leader);
+                if (!active && more) {
+                    const int64_t i = (int64_t)first + __popc(idle & ((1u << lane) - 1u));
+                    const unsigned long long code = i < n_slots ? codes[i] : ~0ull;
+                    if (code == ~0ull) {
+                        more = false;
+                    } else {
+                        bounce_ray(w, code, br, gpix, s);
+                        node = 0;
+                        sp = 0;
+                        steps = 0;
+                        active = a.n_nodes > 0 && br.t_far >= br.t_min;
+                        if (!active) bounce_finish(w, br, gpix, s);
+                    }
+                }
             }
-            const int64_t slot = gpix * a.n_samples + s;
-            for (int c = 0; c < 3; ++c) w.bounce_rgb[3 * slot + c] = w.albedo[c] * lb[c];
+            if (!__any_sync(kAll, active) && !__any_sync(kAll, more)) break;
+            if (active && !lane_step<COUNT>(a, br, s, node, sp, steps, stack, stack_t, err, cnt)) {
+                active = false;
+                bounce_finish(w, br, gpix, s);
+            }
         }
-        __syncwarp();
+    } else {
+        for (;;) {
+            uint32_t tile = 0;
+            if (lane == 0) tile = atomicAdd(a.work, 1u);
+            tile = __shfl_sync(kAll, tile, 0);
+            if ((int64_t)tile * 32 >= n_slots) break;
+            const int64_t i = (int64_t)tile * 32 + lane;
+            const unsigned long long code = i < n_slots ? codes[i] : ~0ull;
+            const bool valid = code != ~0ull;
+            if (!__any_sync(kAll, valid)) break;
+            int64_t gpix = 0;
+            int s = 0;
+            Ray<1> br;
+            if (valid) {
+                bounce_ray(w, code, br, gpix, s);
+            } else {
+                const float p[3] = {0.0f, w.ground_y, 0.0f}, db[3] = {0.0f, 1.0f, 0.0f};
+                set_ray(br, p, db);
+                br.ray_id = 0;
+                br.stream_tag = kTagBounce;
+                br.t_min = w.eps;
+                br.t_max = INFINITY;
+                br.any_hit = false;
+                reset_slots(br);
+                br.t_far = -INFINITY;
+            }
+            trace_own_ray<FMT, COUNT>(a, br, s, stack, stack_t, err, cnt);
+            if (valid) bounce_finish(w, br, gpix, s);
+            __syncwarp();
+        }
     }
     if (err) atomicOr(a.status, err);
     if (COUNT) atomicAdd(w.counters + 3, cnt.node_fetch);
@@ -615,6 +744,9 @@ int64_t wave_slots(const gs_pinhole *cams, int n_views, const gs_scene_extras *e
     int64_t pix = 0;
     for (int v = 0; v < n_views; ++v) pix += (int64_t)cams[v].width * cams[v].height;
     if (pix >= (int64_t)(1 << 24) - 1) return 0;  // the code's pixel field
+    // the bounce pass counts codes in 32 bits, with room for its threads'
+    // last fetches past the end
+    if (pix * p->spp > (int64_t)0xFFFFFFFFll - (1 << 20)) return 0;
     return pix * p->spp;
 }
 
