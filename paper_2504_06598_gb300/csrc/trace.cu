@@ -18,7 +18,9 @@
 //   accept iff xi < alpha (Eq. 4, Fig. 2), replacing the slot (Eq. 6) and
 //        clipping the traversal range to the farthest slot.
 // After the traversal each slot is shaded once (SH colour, Sec. 3.2) or gets
-// the background, and the pixel accumulates the mean of Eq. 7.
+// the background, and the pixel accumulates the mean of Eq. 7. On request
+// every sample's slot {tc, tau, id} is also stored, [pixel][sample], for a
+// gradient launch that reads it instead of tracing again.
 //
 // Float32 formulation of the 1D Gaussian. With o the ray origin, d the unit
 // direction, mu the mean and M = S^-1 R_q^T:
