@@ -178,9 +178,12 @@ constexpr int kWaveMinBlocks = 4;
 // references then kGroupPool entry distances. K: samples a lane carries
 // (slots of its camera and shadow rays); pass j of a lane holds samples
 // j * K .. j * K + K - 1 of its pixel, each with its own keys, outcome and
-// deferred bounce slot, exactly as K lanes with one sample each.
+// deferred bounce slot, exactly as K lanes with one sample each. Built
+// for four 256-thread blocks per SM with every K (eight slots, 16-view
+// frame at spp 8, 16 and 32: 202.4, 381.8 and 737.7 ms against 205.5,
+// 386.9 and 747.4 with three blocks; 423.7 with two at spp 16).
 template <int FMT, int STACK, bool COUNT, int GLG, int K = 1>
-__global__ void __launch_bounds__(kWaveMaxThreads, K >= 8 ? 3 : kWaveMinBlocks)
+__global__ void __launch_bounds__(kWaveMaxThreads, kWaveMinBlocks)
     k_render_views(const WaveArgs w) {
     const TraceArgs &a = w.t;
     const int lane = threadIdx.x & 31;
@@ -806,8 +809,7 @@ gs_status launch_render_views(const gs_bvh *b, const gs_gaussians *g, const gs_p
     philox_round_keys(a.key0, a.key1, a.rk);
     a.stream_tag = p->stream_tag;
     // samples per lane of the camera and shadow pass: 8 from spp 8 to 63
-    // (per-lane packets, the eight-slot kernel at three 256-thread blocks
-    // per SM), 4 at spp 4-7, 2 at spp 2-3; one from spp 64 (grouped), with
+    // (per-lane packets), 4 at spp 4-7, 2 at spp 2-3; one from spp 64 (grouped), with
     // counters, or with the bounce traced inline. Frame of 16 views 256^2
     // to 1080p with ground, four lights and a bounce, one sample per lane
     // -> four -> eight: spp 16 634 -> 472 -> 430 ms, spp 8 -> 269 -> 251,
