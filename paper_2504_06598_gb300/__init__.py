@@ -472,7 +472,9 @@ def render_differentiable(means, log_scales, quats, opacity_logits, sh, sh_degre
     caller has already rebuilt it from these same parameters (several views
     of one parameter state share one rebuild). ``keep_keys=False`` stores
     nothing between forward and backward: the backward traces the winners
-    again."""
+    again; with gradients disabled (``torch.no_grad``) nothing is stored."""
+    if not torch.is_grad_enabled():
+        options = dict(options, keep_keys=False)
     return StochasticRender.apply(means, log_scales, quats, opacity_logits, sh, sh_degree, cam,
                                   options)
 
